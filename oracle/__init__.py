@@ -1,0 +1,166 @@
+"""CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+Plain, slow reference implementations of the per-source queries of the
+fork-processing pattern (Alg. 1, Def. 2.2): Dijkstra SSSP, queue BFS levels,
+FP64 power-iteration PPR and an FP64 sequential push, plus implementation-free
+certificate checks. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / reference legs of ``bench.py`` may import this package. It
+shares no code with the CUDA path and never imports it.
+
+Parity pins (what ties this oracle to something other than itself) live in
+``tests/test_oracle.py``; every function here is pinned there. The PPR
+sequential push (``ppr_push``) is order-dependent by design: its per-vertex
+values are checked only against the error bound, never element by element.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "oracle.c"
+_LIB = _HERE / "_oracle.so"
+_lib = None
+
+UNREACHED = np.uint32(0xFFFFFFFF)
+
+
+def build(force: bool = False) -> Path:
+    """Compile oracle.c (gcc -O2, OpenMP over queries) into an in-tree .so."""
+    if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _LIB.with_suffix(f".{os.getpid()}.tmp")
+        subprocess.run(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", str(_SRC), "-lm",
+                        "-o", str(tmp)], check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(str(_LIB))
+        p = ctypes.c_void_p
+        i32, i64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        lib.orc_set_mutation.argtypes = [ctypes.c_int]
+        lib.orc_num_threads.restype = ctypes.c_int
+        lib.orc_sssp.argtypes = [i64, p, p, p, i32, p]
+        lib.orc_bfs.argtypes = [i64, p, p, i32, p]
+        lib.orc_sssp_batch.argtypes = [i64, p, p, p, i32, p, p]
+        lib.orc_bfs_batch.argtypes = [i64, p, p, i32, p, p]
+        lib.orc_ppr_power.argtypes = [i64, p, p, i32, f64, f64, ctypes.c_int, p]
+        lib.orc_ppr_power_batch.argtypes = [i64, p, p, i32, p, f64, f64, ctypes.c_int, p]
+        lib.orc_ppr_push.argtypes = [i64, p, p, i32, f64, f64, p, p]
+        lib.orc_ppr_push.restype = i64
+        lib.orc_sssp_certificate.argtypes = [i64, p, p, p, i32, p]
+        lib.orc_bfs_certificate.argtypes = [i64, p, p, i32, p]
+        lib.orc_certificate_batch.argtypes = [i64, p, p, p, i32, p, p]
+        lib.orc_certificate_batch.restype = i64
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _csr(g):
+    rp = np.ascontiguousarray(g.row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(g.col, dtype=np.int32)
+    w = None if g.w is None else np.ascontiguousarray(g.w, dtype=np.int32)
+    return rp, col, w
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+def set_mutation(k: int) -> None:
+    """Plant a known mistake (tests only): 1 ignore weights, 2 skip last arc,
+    3 BFS levels start at 1, 4 PPR transposed operand, 5 PPR drops dangling mass."""
+    _load().orc_set_mutation(int(k))
+
+
+def sssp(g, srcs) -> np.ndarray:
+    """Dijkstra distances, query-major uint32[nq, n]; UINT32_MAX = unreachable."""
+    lib = _load()
+    rp, col, w = _csr(g)
+    srcs = np.ascontiguousarray(np.atleast_1d(srcs), dtype=np.int32)
+    out = np.empty((srcs.size, g.n), dtype=np.uint32)
+    rc = lib.orc_sssp_batch(g.n, _p(rp), _p(col), _p(w), srcs.size, _p(srcs), _p(out))
+    if rc != 0:
+        raise RuntimeError(f"orc_sssp_batch failed ({rc})")
+    return out
+
+
+def bfs(g, srcs) -> np.ndarray:
+    """BFS levels, query-major uint32[nq, n]; UINT32_MAX = unreachable."""
+    lib = _load()
+    rp, col, _ = _csr(g)
+    srcs = np.ascontiguousarray(np.atleast_1d(srcs), dtype=np.int32)
+    out = np.empty((srcs.size, g.n), dtype=np.uint32)
+    rc = lib.orc_bfs_batch(g.n, _p(rp), _p(col), srcs.size, _p(srcs), _p(out))
+    if rc != 0:
+        raise RuntimeError(f"orc_bfs_batch failed ({rc})")
+    return out
+
+
+def ppr_power(g, srcs, alpha: float, tol: float = 1e-12, max_iter: int = 100000) -> np.ndarray:
+    """FP64 PPR vectors by power iteration, float64[nq, n]."""
+    lib = _load()
+    rp, col, _ = _csr(g)
+    srcs = np.ascontiguousarray(np.atleast_1d(srcs), dtype=np.int32)
+    out = np.empty((srcs.size, g.n), dtype=np.float64)
+    rc = lib.orc_ppr_power_batch(g.n, _p(rp), _p(col), srcs.size, _p(srcs), alpha, tol, max_iter, _p(out))
+    if rc < 0:
+        raise RuntimeError(f"orc_ppr_power_batch failed ({rc})")
+    return out
+
+
+def ppr_push(g, src: int, alpha: float, eps: float):
+    """FP64 sequential push (largest residual first). Returns (p, r, pushes)."""
+    lib = _load()
+    rp, col, _ = _csr(g)
+    p = np.empty(g.n, dtype=np.float64)
+    r = np.empty(g.n, dtype=np.float64)
+    k = lib.orc_ppr_push(g.n, _p(rp), _p(col), int(src), alpha, eps, _p(p), _p(r))
+    if k < 0:
+        raise RuntimeError(f"orc_ppr_push failed ({k})")
+    return p, r, int(k)
+
+
+def sssp_certificate(g, src: int, dist: np.ndarray) -> int:
+    lib = _load()
+    rp, col, w = _csr(g)
+    d = np.ascontiguousarray(dist, dtype=np.uint32)
+    return int(lib.orc_sssp_certificate(g.n, _p(rp), _p(col), _p(w), int(src), _p(d)))
+
+
+def bfs_certificate(g, src: int, level: np.ndarray) -> int:
+    lib = _load()
+    rp, col, _ = _csr(g)
+    d = np.ascontiguousarray(level, dtype=np.uint32)
+    return int(lib.orc_bfs_certificate(g.n, _p(rp), _p(col), int(src), _p(d)))
+
+
+def certificate_batch(g, srcs, out: np.ndarray, weighted: bool) -> int:
+    """0 if every query's array passes its certificate, else (code << 20) + first failing query."""
+    lib = _load()
+    rp, col, w = _csr(g)
+    srcs = np.ascontiguousarray(np.atleast_1d(srcs), dtype=np.int32)
+    o = np.ascontiguousarray(out, dtype=np.uint32)
+    return int(lib.orc_certificate_batch(g.n, _p(rp), _p(col), _p(w) if weighted else None, srcs.size,
+                                         _p(srcs), _p(o)))
+
+
+def reachable_arcs(g, dist_row: np.ndarray) -> int:
+    """Arcs whose tail is reachable (the edges a sequential Dijkstra/BFS scans)."""
+    deg = np.diff(g.row_ptr)
+    return int(deg[dist_row != UNREACHED].sum())

@@ -1,0 +1,381 @@
+/*
+ * CPU ORACLE -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow, obviously correct reference for the many-source graph queries
+ * of the fork-processing pattern (Alg. 1; Def. 2.2): per-source SSSP, BFS
+ * levels and Personalized PageRank on one CSR graph. Only the test suite, the
+ * smoke check and the benchmark's CPU-baseline leg may load this library; the
+ * CUDA path never calls it and shares no code with it.
+ *
+ * Functions and what they follow:
+ *   orc_sssp      binary-heap (lazy deletion) Dijkstra. An operation <q, v, l>
+ *                 lowers v's path length when l is shorter (Def. 2.3); the
+ *                 sequential algorithm is Dijkstra's (Sec. 4.1, App. A).
+ *   orc_bfs       FIFO-queue BFS levels over out-arcs, weights ignored
+ *                 (Sec. 4.1-4.2: the BFS priority is the lowest level).
+ *   orc_ppr_power FP64 power iteration for pi_s = alpha (I - (1-alpha) P^T)^-1 e_s,
+ *                 P = D^-1 A over out-arcs; a dangling row of P is e_s^T.
+ *                 The paper cites the sequential PPR of Shun et al. without
+ *                 printing alpha, eps or the update rule (Sec. 4.1, 6.1).
+ *   orc_ppr_push  FP64 sequential forward push, highest residual first
+ *                 (the multiset order of Sec. 4.2), non-lazy rule: while
+ *                 r(v) >= eps * max(d(v), 1): p(v) += alpha r(v); each
+ *                 out-neighbour gains (1-alpha) r(v) / d(v) (dangling v returns
+ *                 (1-alpha) r(v) to the source); r(v) = 0. A diagnostic second
+ *                 answer, not the parity target.
+ *   orc_*_certificate  implementation-free checks of a distance / level array.
+ *
+ * Unreachable vertices hold UINT32_MAX. Batches run one query per OpenMP
+ * thread, the paper's best CPU scheme ("t = 1", Sec. 1 and 6.1).
+ *
+ * orc_set_mutation() plants a known mistake (tests use it to show that the
+ * pins catch plausible errors); 0 = none, the default.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static int g_mutation = 0;
+
+void orc_set_mutation(int k) { g_mutation = k; }
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* binary min-heap of (key, vertex)                                          */
+/* ------------------------------------------------------------------------ */
+typedef struct { uint64_t key; int32_t v; } hent;
+typedef struct { hent *a; int64_t n, cap; } heap;
+
+static int heap_push(heap *h, uint64_t key, int32_t v) {
+    if (h->n == h->cap) {
+        int64_t nc = h->cap ? 2 * h->cap : 1024;
+        hent *na = (hent *)realloc(h->a, (size_t)nc * sizeof(hent));
+        if (!na) return -1;
+        h->a = na; h->cap = nc;
+    }
+    int64_t i = h->n++;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (h->a[p].key <= key) break;
+        h->a[i] = h->a[p];
+        i = p;
+    }
+    h->a[i].key = key; h->a[i].v = v;
+    return 0;
+}
+
+static hent heap_pop(heap *h) {
+    hent top = h->a[0];
+    hent last = h->a[--h->n];
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, s = i;
+        uint64_t sk = last.key;
+        if (l < h->n && h->a[l].key < sk) { s = l; sk = h->a[l].key; }
+        if (r < h->n && h->a[r].key < sk) { s = r; }
+        if (s == i) break;
+        h->a[i] = h->a[s];
+        i = s;
+    }
+    if (h->n > 0) h->a[i] = last;
+    return top;
+}
+
+/* ------------------------------------------------------------------------ */
+/* SSSP: Dijkstra (returns 0, or -3 if a finite distance reaches 2^32 - 1)   */
+/* ------------------------------------------------------------------------ */
+int orc_sssp(int64_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *w, int32_t src,
+             uint32_t *dist) {
+    if (src < 0 || src >= n) return -1;
+    uint64_t *d = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+    unsigned char *done = (unsigned char *)calloc((size_t)n, 1);
+    heap h = {0, 0, 0};
+    if (!d || !done) { free(d); free(done); return -2; }
+    for (int64_t v = 0; v < n; ++v) d[v] = UINT64_MAX;
+    d[src] = 0;
+    int rc = heap_push(&h, 0, src);
+    while (rc == 0 && h.n > 0) {
+        hent t = heap_pop(&h);
+        int32_t v = t.v;
+        if (done[v] || t.key != d[v]) continue;
+        done[v] = 1;
+        int64_t end = row_ptr[v + 1];
+        if (g_mutation == 2 && end > row_ptr[v]) end--; /* planted: skips the last arc */
+        for (int64_t e = row_ptr[v]; e < end; ++e) {
+            int32_t u = col[e];
+            uint64_t wt = (w && g_mutation != 1) ? (uint64_t)(uint32_t)w[e] : 1u;
+            uint64_t nd = d[v] + wt;
+            if (nd < d[u]) {
+                d[u] = nd;
+                if (heap_push(&h, nd, u)) { rc = -2; break; }
+            }
+        }
+    }
+    if (rc == 0) {
+        for (int64_t v = 0; v < n; ++v) {
+            if (d[v] == UINT64_MAX) dist[v] = UINT32_MAX;
+            else if (d[v] >= (uint64_t)UINT32_MAX) { rc = -3; dist[v] = UINT32_MAX; }
+            else dist[v] = (uint32_t)d[v];
+        }
+    }
+    free(h.a); free(d); free(done);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* BFS levels with a FIFO queue                                              */
+/* ------------------------------------------------------------------------ */
+int orc_bfs(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t src, uint32_t *level) {
+    if (src < 0 || src >= n) return -1;
+    int32_t *q = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (!q) return -2;
+    for (int64_t v = 0; v < n; ++v) level[v] = UINT32_MAX;
+    int64_t head = 0, tail = 0;
+    level[src] = (g_mutation == 3) ? 1u : 0u; /* planted: levels start at 1 */
+    q[tail++] = src;
+    while (head < tail) {
+        int32_t v = q[head++];
+        for (int64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+            int32_t u = col[e];
+            if (level[u] == UINT32_MAX) {
+                level[u] = level[v] + 1;
+                q[tail++] = u;
+            }
+        }
+    }
+    free(q);
+    return 0;
+}
+
+/* batches: one query per OpenMP thread; out is query-major nq x n */
+int orc_sssp_batch(int64_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *w,
+                   int32_t nq, const int32_t *srcs, uint32_t *out) {
+    int rc = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(min : rc)
+    for (int32_t i = 0; i < nq; ++i) {
+        int r = orc_sssp(n, row_ptr, col, w, srcs[i], out + (size_t)i * (size_t)n);
+        if (r < rc) rc = r;
+    }
+    return rc;
+}
+
+int orc_bfs_batch(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t nq,
+                  const int32_t *srcs, uint32_t *out) {
+    int rc = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(min : rc)
+    for (int32_t i = 0; i < nq; ++i) {
+        int r = orc_bfs(n, row_ptr, col, srcs[i], out + (size_t)i * (size_t)n);
+        if (r < rc) rc = r;
+    }
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* PPR by FP64 power iteration:                                              */
+/*   x_0 = alpha e_s;  x_{k+1} = alpha e_s + (1 - alpha) P^T x_k              */
+/* until ||x_{k+1} - x_k||_1 < tol. Returns the iteration count, or < 0.     */
+/* ------------------------------------------------------------------------ */
+int orc_ppr_power(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t src, double alpha,
+                  double tol, int max_iter, double *pi) {
+    if (src < 0 || src >= n || !(alpha > 0.0 && alpha < 1.0)) return -1;
+    double *x = pi;
+    double *y = (double *)malloc((size_t)n * sizeof(double));
+    if (!y) return -2;
+    for (int64_t v = 0; v < n; ++v) x[v] = 0.0;
+    x[src] = alpha;
+    int it = 0;
+    for (; it < max_iter; ++it) {
+        for (int64_t v = 0; v < n; ++v) y[v] = 0.0;
+        /* y = P^T x, P = D^-1 A (row v spreads x[v] / d(v) over its out-arcs) */
+        for (int64_t v = 0; v < n; ++v) {
+            int64_t d = row_ptr[v + 1] - row_ptr[v];
+            if (x[v] == 0.0) continue;
+            if (d == 0) {
+                if (g_mutation != 5) y[src] += x[v]; /* dangling row = e_s^T (planted 5 drops it) */
+                continue;
+            }
+            double share = x[v] / (double)d;
+            for (int64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+                if (g_mutation == 4) y[v] += x[col[e]] / (double)d; /* planted: transposed operand */
+                else y[col[e]] += share;
+            }
+        }
+        double diff = 0.0;
+        for (int64_t v = 0; v < n; ++v) {
+            double nv = (1.0 - alpha) * y[v] + (v == src ? alpha : 0.0);
+            diff += fabs(nv - x[v]);
+            x[v] = nv;
+        }
+        if (diff < tol) { ++it; break; }
+    }
+    free(y);
+    return it;
+}
+
+int orc_ppr_power_batch(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t nq,
+                        const int32_t *srcs, double alpha, double tol, int max_iter, double *out) {
+    int rc = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(min : rc)
+    for (int32_t i = 0; i < nq; ++i) {
+        int r = orc_ppr_power(n, row_ptr, col, srcs[i], alpha, tol, max_iter, out + (size_t)i * (size_t)n);
+        if (r < rc) rc = r;
+    }
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* PPR by FP64 sequential forward push, largest residual first.              */
+/* Returns the number of pushes, or < 0.                                     */
+/* ------------------------------------------------------------------------ */
+typedef struct { double key; int32_t v; } mxent;
+
+static void mx_push(mxent *a, int64_t *n, double key, int32_t v) {
+    int64_t i = (*n)++;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (a[p].key >= key) break;
+        a[i] = a[p];
+        i = p;
+    }
+    a[i].key = key; a[i].v = v;
+}
+
+static mxent mx_pop(mxent *a, int64_t *n) {
+    mxent top = a[0], last = a[--(*n)];
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, s = i;
+        double sk = last.key;
+        if (l < *n && a[l].key > sk) { s = l; sk = a[l].key; }
+        if (r < *n && a[r].key > sk) { s = r; }
+        if (s == i) break;
+        a[i] = a[s];
+        i = s;
+    }
+    if (*n > 0) a[i] = last;
+    return top;
+}
+
+int64_t orc_ppr_push(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t src, double alpha,
+                     double eps, double *p, double *r) {
+    if (src < 0 || src >= n || !(alpha > 0.0 && alpha < 1.0) || !(eps > 0.0)) return -1;
+    for (int64_t v = 0; v < n; ++v) { p[v] = 0.0; r[v] = 0.0; }
+    r[src] = 1.0;
+    /* lazy max-heap of (residual at insertion, v); capacity grows as needed */
+    int64_t cap = 1024, hn = 0, pushes = 0;
+    mxent *hp = (mxent *)malloc((size_t)cap * sizeof(mxent));
+    if (!hp) return -2;
+    mx_push(hp, &hn, 1.0, src);
+    while (hn > 0) {
+        mxent t = mx_pop(hp, &hn);
+        int32_t v = t.v;
+        int64_t d = row_ptr[v + 1] - row_ptr[v];
+        double thr = eps * (double)(d > 0 ? d : 1);
+        if (t.key != r[v] || r[v] < thr) continue; /* stale entry */
+        double rho = r[v];
+        r[v] = 0.0;
+        p[v] += alpha * rho;
+        ++pushes;
+        if (hn + d + 1 >= cap) {
+            while (hn + d + 1 >= cap) cap *= 2;
+            mxent *nh = (mxent *)realloc(hp, (size_t)cap * sizeof(mxent));
+            if (!nh) { free(hp); return -2; }
+            hp = nh;
+        }
+        if (d == 0) {
+            r[src] += (1.0 - alpha) * rho;
+            double ts = eps * (double)((row_ptr[src + 1] - row_ptr[src]) > 0 ? (row_ptr[src + 1] - row_ptr[src]) : 1);
+            if (r[src] >= ts) mx_push(hp, &hn, r[src], src);
+            continue;
+        }
+        double inc = (1.0 - alpha) * rho / (double)d;
+        for (int64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+            int32_t u = col[e];
+            r[u] += inc;
+            int64_t du = row_ptr[u + 1] - row_ptr[u];
+            if (r[u] >= eps * (double)(du > 0 ? du : 1)) mx_push(hp, &hn, r[u], u);
+        }
+    }
+    free(hp);
+    return pushes;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Certificates (no shortest-path computation inside):                       */
+/*   SSSP (w >= 1): d(s) = 0; every arc (u,v) with d(u) finite has           */
+/*   d(v) <= d(u) + w; every finite v != s has an arc (u,v) with             */
+/*   d(v) = d(u) + w; d(v) finite iff v is reachable from s.                 */
+/* With positive weights these conditions determine d exactly. BFS is the    */
+/* same check with unit weights. Returns 0 if valid, else a code naming the  */
+/* failed condition (1 source, 2 edge slack, 3 no parent, 4 reachability).   */
+/* ------------------------------------------------------------------------ */
+static int certificate(int64_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *w,
+                       int32_t src, const uint32_t *d) {
+    if (d[src] != 0) return 1;
+    unsigned char *has_parent = (unsigned char *)calloc((size_t)n, 1);
+    unsigned char *seen = (unsigned char *)calloc((size_t)n, 1);
+    int32_t *q = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (!has_parent || !seen || !q) { free(has_parent); free(seen); free(q); return -2; }
+    int rc = 0;
+    for (int64_t u = 0; u < n && rc == 0; ++u) {
+        if (d[u] == UINT32_MAX) continue;
+        for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+            int32_t v = col[e];
+            uint64_t cand = (uint64_t)d[u] + (w ? (uint64_t)(uint32_t)w[e] : 1u);
+            if ((uint64_t)d[v] > cand) { rc = 2; break; }
+            if ((uint64_t)d[v] == cand) has_parent[v] = 1;
+        }
+    }
+    for (int64_t v = 0; v < n && rc == 0; ++v)
+        if (v != src && d[v] != UINT32_MAX && !has_parent[v]) rc = 3;
+    if (rc == 0) {
+        int64_t head = 0, tail = 0;
+        seen[src] = 1; q[tail++] = src;
+        while (head < tail) {
+            int32_t v = q[head++];
+            for (int64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e)
+                if (!seen[col[e]]) { seen[col[e]] = 1; q[tail++] = col[e]; }
+        }
+        for (int64_t v = 0; v < n && rc == 0; ++v)
+            if ((seen[v] != 0) != (d[v] != UINT32_MAX)) rc = 4;
+    }
+    free(has_parent); free(seen); free(q);
+    return rc;
+}
+
+int orc_sssp_certificate(int64_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *w,
+                         int32_t src, const uint32_t *dist) {
+    return certificate(n, row_ptr, col, w, src, dist);
+}
+
+int orc_bfs_certificate(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t src,
+                        const uint32_t *level) {
+    return certificate(n, row_ptr, col, NULL, src, level);
+}
+
+/* certificate over a query-major batch; returns the first failing query's code * 2^20 + q, else 0 */
+int64_t orc_certificate_batch(int64_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *w,
+                              int32_t nq, const int32_t *srcs, const uint32_t *out) {
+    int64_t first = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t i = 0; i < nq; ++i) {
+        int r = certificate(n, row_ptr, col, w, srcs[i], out + (size_t)i * (size_t)n);
+        if (r != 0) {
+#pragma omp critical
+            if (first == 0) first = ((int64_t)r << 20) + i;
+        }
+    }
+    return first;
+}

@@ -1,0 +1,79 @@
+"""Seeded input generators: determinism and the structural facts the workloads rely on."""
+import hashlib
+
+import numpy as np
+
+from paper_2103_14915_gb300 import inputs as I
+
+
+def digest(g):
+    h = hashlib.sha256()
+    h.update(g.row_ptr.tobytes())
+    h.update(g.col.tobytes())
+    if g.w is not None:
+        h.update(g.w.tobytes())
+    return h.hexdigest()
+
+
+def check_simple(g, symmetric):
+    rp, col = g.row_ptr, g.col
+    assert rp[0] == 0 and rp[-1] == col.size and np.all(np.diff(rp) >= 0)
+    src = np.repeat(np.arange(g.n), np.diff(rp))
+    assert np.all(col >= 0) and np.all(col < g.n)
+    assert not np.any(src == col), "self-loop"
+    key = src.astype(np.int64) * g.n + col
+    assert np.all(np.diff(key) > 0), "rows sorted, no duplicate arcs"
+    if symmetric:
+        rkey = np.sort(col.astype(np.int64) * g.n + src)
+        assert np.array_equal(rkey, key)
+        if g.w is not None:
+            order = np.argsort(col.astype(np.int64) * g.n + src)
+            assert np.array_equal(g.w[order], g.w)
+
+
+def test_rmat_deterministic_and_simple():
+    a = I.rmat(12, 16, seed=7, weights=(1, 255))
+    b = I.rmat(12, 16, seed=7, weights=(1, 255))
+    c = I.rmat(12, 16, seed=8, weights=(1, 255))
+    assert digest(a) == digest(b) != digest(c)
+    check_simple(a, symmetric=True)
+    assert a.w.min() >= 1 and a.w.max() <= 255
+    deg = a.out_degree()
+    assert deg.max() > 20 * deg.mean(), "power-law hubs"
+    assert a.m <= 2 * 16 * 4096
+
+
+def test_rmat_directed():
+    g = I.rmat(11, 8, seed=3, directed=True)
+    check_simple(g, symmetric=False)
+    assert (g.out_degree() == 0).any()
+
+
+def test_grid_structure():
+    g = I.grid(64, 80, 500, 100, seed=5, weights=(100, 10000))
+    check_simple(g, symmetric=True)
+    n4 = 2 * 64 * 80 - 64 - 80
+    und = g.m // 2
+    assert 0.93 * n4 < und < 0.97 * n4 + 0.012 * g.n
+    assert g.w.min() >= 100 and g.w.max() <= 10000
+    r, c = np.divmod(np.repeat(np.arange(g.n), g.out_degree()), 80)
+    rr, cc = np.divmod(g.col, 80)
+    assert np.all(np.abs(r - rr) <= 1) and np.all(np.abs(c - cc) <= 1), "local edges only"
+
+
+def test_sources():
+    g = I.rmat(12, 8, seed=2)
+    s = I.sources_uniform(g, 500, 11)
+    assert len(set(s.tolist())) == 500 and np.all(g.out_degree()[s] >= 1)
+    assert np.array_equal(s, I.sources_uniform(g, 500, 11))
+    t = I.sources_logdeg(g, 200, 4)
+    assert len(set(t.tolist())) == 200
+    b = np.floor(np.log2(g.out_degree()[t])).astype(int)
+    counts = np.bincount(b)
+    avail = np.bincount(np.floor(np.log2(g.out_degree()[g.out_degree() > 0])).astype(int))
+    full = counts[counts > 0]
+    # water-filling: every bucket either gets the common share or is taken whole
+    share = full.max()
+    for k, cnt in enumerate(counts):
+        if avail[k]:
+            assert cnt == min(avail[k], share) or cnt == share - 1
