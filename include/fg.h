@@ -1,0 +1,193 @@
+/*
+ * fg.h -- C ABI of the buffered fork-processing engine (sm_103a).
+ *
+ * The fork-processing pattern (FPP) launches many independent single-source
+ * queries on one graph (Alg. 1; Def. 2.2). This library runs a batch of such
+ * queries -- exact integer SSSP, BFS levels, or forward-push Personalized
+ * PageRank -- in the buffered style of Alg. 2: the graph is split into
+ * partitions (Def. 2.1), every query's pending operations <q, v, val>
+ * (Def. 2.3) are kept in per-(partition, query) buffers, and all buffered
+ * work on a partition is processed while that partition's data is on chip.
+ *
+ * Conventions for every call:
+ *   - Vertex ids are the caller's original ids in [0, n).
+ *   - Outputs are query-major: row i (n entries) belongs to src[i].
+ *   - Unless opts->host_io is set, src and every output are DEVICE pointers
+ *     owned by the caller, and the call is asynchronous on `stream` (a
+ *     cudaStream_t, NULL = the legacy default stream). Results are valid
+ *     after fg_sync(stream) returns FG_OK.
+ *   - Errors that the host can detect (null or misaligned pointers, bad
+ *     sizes, source ids out of range, negative weights) are returned at once
+ *     and nothing is enqueued. Errors found on the device (watchdog timeout,
+ *     distance overflow, CUDA faults) are returned by fg_sync.
+ *   - fg_last_error() gives a message for the last failing call on the
+ *     calling thread.
+ *   - Batches on one graph are serialised in stream order by the library
+ *     (each batch waits for the previous batch on the same graph), because
+ *     they share the graph's device workspace.
+ */
+#ifndef FG_H
+#define FG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FG_OK = 0,
+    FG_ERR_INVALID_ARG = 1,   /* bad argument, detected on the host; nothing enqueued */
+    FG_ERR_OOM = 2,           /* device or host allocation failed / HBM budget exceeded */
+    FG_ERR_CUDA = 3,          /* a CUDA call failed (message in fg_last_error) */
+    FG_ERR_TIMEOUT = 4,       /* device watchdog: max_rounds or a barrier wait limit was hit */
+    FG_ERR_BIN_OVERFLOW = 5,  /* operation buffers could not hold the work (not raised: ops spill losslessly) */
+    FG_ERR_OVERFLOW = 6,      /* an SSSP distance reached 2^32 - 1 (saturated) */
+    FG_ERR_UNSUPPORTED = 7    /* size beyond the supported range (e.g. m >= 2^32) */
+} fg_status;
+
+typedef struct fg_graph fg_graph;
+
+/* fg_graph_create flags */
+#define FG_DEVICE_PTRS 0x1u   /* row_ptr, col, w are device pointers (the library copies them) */
+
+/* partitioners (Def. 2.1: a division of V into |P| disjoint vertex sets) */
+enum {
+    FG_PART_AUTO = 0,    /* GROW when the id order has little locality, else RANGE */
+    FG_PART_RANGE = 1,   /* contiguous id ranges [i*S, (i+1)*S): the paper's equal-vertex split */
+    FG_PART_GROW = 2     /* breadth-first region growing to S vertices (stand-in for METIS) */
+};
+
+typedef struct {
+    uint32_t struct_size;        /* sizeof(fg_graph_opts) */
+    int32_t partition_method;    /* FG_PART_* */
+    int32_t partition_vertices;  /* S, a power of two in [32, 4096]; 0 = from the on-chip budget */
+} fg_graph_opts;
+
+/* inter-partition scheduling (Sec. 5.2) */
+enum { FG_SCHED_FIFO = 0, FG_SCHED_PRIORITY = 1 };
+/* execution form */
+enum { FG_MODE_BUFFERED = 0, FG_MODE_PLAIN = 1 };
+
+typedef struct {
+    uint32_t struct_size;   /* sizeof(fg_opts); fields past it keep their defaults */
+    int32_t mode;           /* FG_MODE_BUFFERED (default); FG_MODE_PLAIN runs one query at a
+                               time with ordinary whole-graph frontier kernels (the baseline) */
+    int32_t sched;          /* FG_SCHED_FIFO (default, Sec. 5.2) or FG_SCHED_PRIORITY: each
+                               round processes a query's buffers whose best value lies within
+                               sched_window of that query's best pending value */
+    uint32_t sched_window;  /* window of FG_SCHED_PRIORITY (SSSP/BFS value units); 0 = 8 * delta */
+    uint32_t delta;         /* yield heuristic 2 (Sec. 5.1): within one visit a query processes
+                               values below (first value + delta); the rest stays buffered.
+                               0 = no limit */
+    uint32_t bucket;        /* in-visit near/far width: values are relaxed in windows of this
+                               width (Delta-stepping order inside a partition). 0 = none */
+    uint64_t yield_edges;   /* yield heuristic 1 (Sec. 5.1): arcs one query may scan in one
+                               visit before yielding. 0 = no limit */
+    uint32_t max_rounds;    /* watchdog: rounds before FG_ERR_TIMEOUT. 0 = 1,000,000 */
+    uint32_t watchdog_ms;   /* watchdog: longest wait at a device-wide barrier. 0 = 30,000 */
+    uint64_t emit_capacity; /* operations one round may buffer; beyond it, work spills to
+                               per-partition pending bitmaps (lossless). 0 = automatic */
+    int32_t host_io;        /* 1: src and outputs are HOST pointers; the call copies them and
+                               completes before returning (fg_sync still reports status) */
+    int32_t query_batch;    /* queries per device launch; 0 = all (bounded by workspace) */
+} fg_opts;
+
+/* counters of the last completed batch on a graph (read by fg_stats after fg_sync) */
+typedef struct {
+    uint64_t rounds;        /* Alg. 2 loop iterations (sum over launches) */
+    uint64_t visits;        /* (partition, query) buffers processed */
+    uint64_t edges;         /* arcs scanned by the relax/push kernels */
+    uint64_t ops;           /* operations buffered */
+    uint64_t spills;        /* expansions deferred because the op arena was full */
+    uint64_t yields;        /* visits that left work behind (yield or budget) */
+    uint64_t launches;      /* kernels launched by the batch */
+    uint64_t max_round_ops; /* most operations buffered in one round */
+} fg_stats_t;
+
+typedef struct {
+    int64_t n, m;
+    int32_t partition_vertices;  /* S */
+    int32_t num_partitions;      /* |P| */
+    int32_t partition_method;    /* FG_PART_RANGE or FG_PART_GROW (after AUTO) */
+    int32_t weighted;
+    int64_t cut_arcs;            /* arcs whose endpoints lie in different partitions */
+    int64_t device_bytes;        /* graph bytes resident on the device */
+} fg_graph_info_t;
+
+/* Fill *o with the defaults. */
+void fg_default_opts(fg_opts *o);
+void fg_default_graph_opts(fg_graph_opts *o);
+
+/*
+ * Build a device graph from CSR (Ligra-style storage, Sec. 3.1): row_ptr has
+ * n + 1 entries (row_ptr[0] = 0, non-decreasing, row_ptr[n] = m), col has m
+ * vertex ids in [0, n), w has m int32 weights >= 0 or is NULL (unit weights).
+ * Undirected graphs store both arcs of every edge (Sec. 2.1). The caller's
+ * arrays are copied; the caller keeps ownership. Requires 1 <= n < 2^31 and
+ * m < 2^32. Partitions the vertices (Def. 2.1) and stores the graph
+ * partition-major on the device. Synchronous. *out receives the handle.
+ */
+fg_status fg_graph_create(int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
+                          const int32_t *w, uint32_t flags, fg_graph **out);
+
+/* As fg_graph_create, with partitioning options (NULL = defaults). */
+fg_status fg_graph_create_ex(int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
+                             const int32_t *w, uint32_t flags, const fg_graph_opts *gopts,
+                             fg_graph **out);
+
+/* Release a graph and its workspace. Waits for its batches to finish. NULL is allowed. */
+fg_status fg_graph_destroy(fg_graph *g);
+
+/* Sizes and partition facts of a graph. */
+fg_status fg_graph_info(const fg_graph *g, fg_graph_info_t *info);
+
+/*
+ * nq single-source shortest-path queries (Def. 2.3: an operation <q, v, l>
+ * lowers v's path length to l when l is shorter). dist_out: uint32[nq * n],
+ * exact distances; UINT32_MAX = unreachable. src: int32[nq] (duplicates are
+ * allowed). Unweighted graphs use weight 1.
+ */
+fg_status fg_sssp_batch(fg_graph *g, const int32_t *src, int32_t nq, uint32_t *dist_out,
+                        void *stream, const fg_opts *opts);
+
+/* nq BFS queries: level_out uint32[nq * n], hop levels; UINT32_MAX = unreachable. */
+fg_status fg_bfs_batch(fg_graph *g, const int32_t *src, int32_t nq, uint32_t *level_out,
+                       void *stream, const fg_opts *opts);
+
+/*
+ * nq Personalized PageRank queries by forward push (non-lazy rule): a vertex
+ * v with residual r(v) >= eps * max(deg(v), 1) moves alpha * r(v) into its
+ * estimate and spreads (1 - alpha) * r(v) / deg(v) to each out-neighbour
+ * (a dangling vertex returns (1 - alpha) * r(v) to the source); r(v) = 0.
+ * Estimates are FP32 with compensated (Kahan) accumulation; residuals FP32.
+ * p_out float[nq * n] (required), r_out float[nq * n] (may be NULL),
+ * mass_out double[nq] (may be NULL): sum(p) + sum(r) per query in FP64.
+ * Requires 0 < alpha < 1 and eps > 0.
+ */
+fg_status fg_ppr_batch(fg_graph *g, const int32_t *src, int32_t nq, float alpha, float eps,
+                       float *p_out, float *r_out, double *mass_out, void *stream,
+                       const fg_opts *opts);
+
+/* Wait for the work enqueued on `stream`; return the first device-side error of its batches. */
+fg_status fg_sync(void *stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *fg_last_error(void);
+
+/* Counters of the last batch on g that fg_sync has completed. */
+fg_status fg_stats(const fg_graph *g, fg_stats_t *out);
+
+/*
+ * Host-only partitioner, exposed for inspection: writes perm[i] = original id
+ * of internal vertex i (partition j holds internal ids [j*S, (j+1)*S)).
+ * Makes no CUDA call. method is FG_PART_RANGE or FG_PART_GROW.
+ */
+fg_status fg_partition_plan(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t method,
+                            int32_t partition_vertices, int32_t *perm);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FG_H */

@@ -1,0 +1,104 @@
+// Internal structures shared by the host runtime and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/fg.h"
+
+namespace fg {
+
+enum QType : int { Q_SSSP = 0, Q_BFS = 1, Q_PPR = 2 };
+
+constexpr uint32_t kInf = 0xFFFFFFFFu;
+constexpr uint32_t kInvalidKey = 0xFFFFFFFFu;
+
+// Graph in partition-major ("internal") vertex order. Partition j holds the
+// internal ids [j*S, (j+1)*S); S = 1 << slog2.
+struct DevGraph {
+  int32_t n = 0;
+  int32_t slog2 = 0;
+  int32_t S = 0;
+  int32_t nparts = 0;
+  uint64_t m = 0;
+  const uint32_t *rp = nullptr;    // [n+1] arc offsets
+  const uint32_t *adj = nullptr;   // [m] internal target ids
+  const uint32_t *wt = nullptr;    // [m] weights, or null (unit)
+  const int32_t *orig = nullptr;   // [n] internal -> original id, or null (identity)
+  const int32_t *intl = nullptr;   // [n] original -> internal id, or null (identity)
+};
+
+// Device control block of one batch launch (zeroed before each launch).
+struct Ctrl {
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  int status;                 // fg_status raised on the device (0 = ok)
+  int abort;                  // set with status: every block leaves at its next check
+  unsigned int item_next;     // work-claiming counter of the current round
+  unsigned int pad0;
+  unsigned long long e_cursor;  // operations reserved in the arena this round
+  unsigned long long rounds, visits, edges, ops, spills, yields, max_round_ops;
+};
+
+struct EngineArgs {
+  DevGraph g;
+  int qtype = Q_SSSP;
+  int32_t nq = 0;
+  const int32_t *src = nullptr;   // [nq] original ids (device)
+  // query state, query-major [nq][n], original vertex order
+  uint32_t *dist = nullptr;       // SSSP / BFS
+  float *pr_p = nullptr;          // PPR estimate
+  float *pr_r = nullptr;          // PPR residual
+  float *pr_c = nullptr;          // PPR Kahan compensation
+  float alpha = 0.f, eps = 0.f;
+  // per-(partition, query) buffers, key = p * nq + q
+  uint32_t *cnt = nullptr;        // [K] operations buffered this round
+  uint32_t *prio = nullptr;       // [K] best pending value (SSSP/BFS)
+  uint32_t *dirty = nullptr;      // [K] pending bitmap non-empty
+  uint32_t *cur = nullptr;        // [K] scatter cursor
+  uint32_t *pend = nullptr;       // [K][S/32] deferred vertices
+  uint32_t *qbest = nullptr;      // [nq] best pending value per query (priority scheduling)
+  uint4 *items = nullptr;         // [K] {key, offset, count, flags}
+  uint32_t *iprio = nullptr;      // [K] best value of each work item (priority carry-over)
+  unsigned long long *blocksum = nullptr;  // [grid] (ops << 32 | items) per block
+  // operation arena (append order) and bins (key order)
+  uint32_t *e_key = nullptr;
+  uint2 *e_op = nullptr;
+  uint2 *b_op = nullptr;
+  uint64_t e_cap = 0;
+  Ctrl *ctrl = nullptr;
+  // options
+  uint32_t delta = 0, bucket = 0, sched = 0, sched_window = 0;
+  uint64_t yield_edges = 0;
+  uint32_t max_rounds = 0;
+  uint64_t watchdog_ns = 0;
+};
+
+struct PlainArgs {
+  DevGraph g;
+  int qtype = Q_SSSP;
+  int32_t q = 0;
+  int32_t nq = 0;
+  uint32_t *out_u32 = nullptr;    // row base of query q (original order)
+  const int32_t *src = nullptr;   // [nq] original source ids (device)
+  float *out_p = nullptr, *out_r = nullptr, *out_c = nullptr;  // row bases (original order)
+  uint32_t *dist = nullptr;       // [n] scratch, internal order
+  float *rr = nullptr, *pp = nullptr, *cc = nullptr;  // [n] scratch, internal order
+  uint32_t *stamp = nullptr;      // [n]
+  uint32_t *front[2] = {nullptr, nullptr};  // [n] each
+  uint32_t *sizes = nullptr;      // [3]
+  float alpha = 0.f, eps = 0.f;
+  uint32_t max_rounds = 0;
+  uint64_t watchdog_ns = 0;
+  Ctrl *ctrl = nullptr;
+};
+
+// kernel launchers (fg_engine.cu / fg_plain.cu); return the CUDA error of the launch
+cudaError_t engine_grid_size(int qtype, int S, int *blocks, int *threads, size_t *smem);
+cudaError_t launch_engine(const EngineArgs &a, int blocks, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_ppr_finalize(const EngineArgs &a, double *mass, float *r_out, cudaStream_t s);
+cudaError_t plain_grid_size(int *blocks, int *threads);
+cudaError_t launch_plain(const PlainArgs &a, int blocks, int threads, cudaStream_t s);
+
+}  // namespace fg

@@ -1,0 +1,210 @@
+"""Thin ctypes binding of the C ABI in ``include/fg.h`` (argument marshalling only).
+
+Every function has the name of its C entry point and returns the C status code
+(``FG_OK`` = 0); :func:`check` turns a code into an exception carrying
+``fg_last_error()``. Buffers may be torch tensors (device memory, via
+``data_ptr()``), numpy arrays (host memory, for ``host_io`` calls) or raw
+integer addresses. Streams are ``torch.cuda.Stream`` objects, raw handles, or
+None for the legacy default stream.
+
+The shared library is built in-tree by :func:`paper_2103_14915_gb300.build.build`;
+loading fails loudly if it is missing -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+_LIB_PATH = Path(__file__).resolve().parent / "libfg.so"
+_lib = None
+
+FG_OK = 0
+FG_ERR_INVALID_ARG = 1
+FG_ERR_OOM = 2
+FG_ERR_CUDA = 3
+FG_ERR_TIMEOUT = 4
+FG_ERR_BIN_OVERFLOW = 5
+FG_ERR_OVERFLOW = 6
+FG_ERR_UNSUPPORTED = 7
+STATUS_NAMES = {0: "FG_OK", 1: "FG_ERR_INVALID_ARG", 2: "FG_ERR_OOM", 3: "FG_ERR_CUDA", 4: "FG_ERR_TIMEOUT",
+                5: "FG_ERR_BIN_OVERFLOW", 6: "FG_ERR_OVERFLOW", 7: "FG_ERR_UNSUPPORTED"}
+
+FG_DEVICE_PTRS = 0x1
+FG_PART_AUTO, FG_PART_RANGE, FG_PART_GROW = 0, 1, 2
+FG_SCHED_FIFO, FG_SCHED_PRIORITY = 0, 1
+FG_MODE_BUFFERED, FG_MODE_PLAIN = 0, 1
+
+
+class fg_graph_opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("partition_method", ctypes.c_int32),
+                ("partition_vertices", ctypes.c_int32)]
+
+
+class fg_opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("mode", ctypes.c_int32), ("sched", ctypes.c_int32),
+                ("sched_window", ctypes.c_uint32), ("delta", ctypes.c_uint32), ("bucket", ctypes.c_uint32),
+                ("yield_edges", ctypes.c_uint64), ("max_rounds", ctypes.c_uint32),
+                ("watchdog_ms", ctypes.c_uint32), ("emit_capacity", ctypes.c_uint64),
+                ("host_io", ctypes.c_int32), ("query_batch", ctypes.c_int32)]
+
+
+class fg_stats_t(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in
+                ("rounds", "visits", "edges", "ops", "spills", "yields", "launches", "max_round_ops")]
+
+
+class fg_graph_info_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("partition_vertices", ctypes.c_int32),
+                ("num_partitions", ctypes.c_int32), ("partition_method", ctypes.c_int32),
+                ("weighted", ctypes.c_int32), ("cut_arcs", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
+EXPORTS = ("fg_default_opts", "fg_default_graph_opts", "fg_graph_create", "fg_graph_create_ex",
+           "fg_graph_destroy", "fg_graph_info", "fg_sssp_batch", "fg_bfs_batch", "fg_ppr_batch", "fg_sync",
+           "fg_last_error", "fg_stats", "fg_partition_plan")
+
+
+def lib_path() -> Path:
+    return _LIB_PATH
+
+
+def load():
+    """Load libfg.so (built in-tree). Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not _LIB_PATH.exists():
+        raise RuntimeError(f"{_LIB_PATH} is missing: build it with paper_2103_14915_gb300.build.build()")
+    lib = ctypes.CDLL(str(_LIB_PATH))
+    vp, i32, i64, u32, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_float
+    lib.fg_default_opts.argtypes = [ctypes.POINTER(fg_opts)]
+    lib.fg_default_opts.restype = None
+    lib.fg_default_graph_opts.argtypes = [ctypes.POINTER(fg_graph_opts)]
+    lib.fg_default_graph_opts.restype = None
+    lib.fg_graph_create.argtypes = [i64, i64, vp, vp, vp, u32, ctypes.POINTER(vp)]
+    lib.fg_graph_create_ex.argtypes = [i64, i64, vp, vp, vp, u32, ctypes.POINTER(fg_graph_opts), ctypes.POINTER(vp)]
+    lib.fg_graph_destroy.argtypes = [vp]
+    lib.fg_graph_info.argtypes = [vp, ctypes.POINTER(fg_graph_info_t)]
+    lib.fg_sssp_batch.argtypes = [vp, vp, i32, vp, vp, ctypes.POINTER(fg_opts)]
+    lib.fg_bfs_batch.argtypes = [vp, vp, i32, vp, vp, ctypes.POINTER(fg_opts)]
+    lib.fg_ppr_batch.argtypes = [vp, vp, i32, f32, f32, vp, vp, vp, vp, ctypes.POINTER(fg_opts)]
+    lib.fg_sync.argtypes = [vp]
+    lib.fg_last_error.argtypes = []
+    lib.fg_last_error.restype = ctypes.c_char_p
+    lib.fg_stats.argtypes = [vp, ctypes.POINTER(fg_stats_t)]
+    lib.fg_partition_plan.argtypes = [i64, vp, vp, i32, i32, vp]
+    for name in ("fg_graph_create", "fg_graph_create_ex", "fg_graph_destroy", "fg_graph_info", "fg_sssp_batch",
+                 "fg_bfs_batch", "fg_ppr_batch", "fg_sync", "fg_stats", "fg_partition_plan"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class FGError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def fg_last_error() -> str:
+    return load().fg_last_error().decode()
+
+
+def check(status: int) -> None:
+    if status != FG_OK:
+        raise FGError(status, fg_last_error())
+
+
+def _ptr(x):
+    """Address of a torch tensor, numpy array, ctypes object or int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    return ctypes.addressof(x)
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def fg_default_opts(**overrides) -> fg_opts:
+    o = fg_opts()
+    load().fg_default_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def fg_default_graph_opts(**overrides) -> fg_graph_opts:
+    o = fg_graph_opts()
+    load().fg_default_graph_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def fg_graph_create(n, m, row_ptr, col, w=None, flags=0):
+    """Returns (status, handle)."""
+    h = ctypes.c_void_p()
+    st = load().fg_graph_create(n, m, _ptr(row_ptr), _ptr(col), _ptr(w), flags, ctypes.byref(h))
+    return st, h.value
+
+
+def fg_graph_create_ex(n, m, row_ptr, col, w=None, flags=0, gopts=None):
+    """Returns (status, handle)."""
+    h = ctypes.c_void_p()
+    st = load().fg_graph_create_ex(n, m, _ptr(row_ptr), _ptr(col), _ptr(w), flags,
+                                   ctypes.byref(gopts) if gopts is not None else None, ctypes.byref(h))
+    return st, h.value
+
+
+def fg_graph_destroy(g) -> int:
+    return load().fg_graph_destroy(g)
+
+
+def fg_graph_info(g):
+    """Returns (status, fg_graph_info_t)."""
+    info = fg_graph_info_t()
+    return load().fg_graph_info(g, ctypes.byref(info)), info
+
+
+def fg_sssp_batch(g, src, nq, dist_out, stream=None, opts=None) -> int:
+    return load().fg_sssp_batch(g, _ptr(src), nq, _ptr(dist_out), _stream(stream),
+                                ctypes.byref(opts) if opts is not None else None)
+
+
+def fg_bfs_batch(g, src, nq, level_out, stream=None, opts=None) -> int:
+    return load().fg_bfs_batch(g, _ptr(src), nq, _ptr(level_out), _stream(stream),
+                               ctypes.byref(opts) if opts is not None else None)
+
+
+def fg_ppr_batch(g, src, nq, alpha, eps, p_out, r_out=None, mass_out=None, stream=None, opts=None) -> int:
+    return load().fg_ppr_batch(g, _ptr(src), nq, alpha, eps, _ptr(p_out), _ptr(r_out), _ptr(mass_out),
+                               _stream(stream), ctypes.byref(opts) if opts is not None else None)
+
+
+def fg_sync(stream=None) -> int:
+    return load().fg_sync(_stream(stream))
+
+
+def fg_stats(g):
+    """Returns (status, fg_stats_t)."""
+    s = fg_stats_t()
+    return load().fg_stats(g, ctypes.byref(s)), s
+
+
+def fg_partition_plan(n, row_ptr, col, method, partition_vertices, perm_out) -> int:
+    return load().fg_partition_plan(n, _ptr(row_ptr), _ptr(col), method, partition_vertices, _ptr(perm_out))

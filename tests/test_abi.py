@@ -1,0 +1,127 @@
+"""C ABI checks that need no GPU: the library builds and loads, exports every
+symbol include/fg.h declares, rejects bad arguments on the host before any CUDA
+call, and its host-only partitioner returns valid partitions."""
+import ctypes
+import re
+
+import numpy as np
+import pytest
+
+from paper_2103_14915_gb300 import build as fgbuild
+from paper_2103_14915_gb300 import fg, inputs
+
+HEADER = fgbuild.ROOT / "include" / "fg.h"
+
+
+@pytest.fixture(scope="module")
+def lib():
+    fgbuild.build()
+    return fg.load()
+
+
+def declared_functions():
+    text = HEADER.read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fg_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 13
+    for name in names:
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+    assert set(names) == set(fg.EXPORTS)
+
+
+def test_struct_sizes_match_header(lib):
+    o = fg.fg_default_opts()
+    assert o.struct_size == ctypes.sizeof(fg.fg_opts)
+    go = fg.fg_default_graph_opts()
+    assert go.struct_size == ctypes.sizeof(fg.fg_graph_opts)
+    assert go.partition_method == fg.FG_PART_AUTO and o.mode == fg.FG_MODE_BUFFERED
+
+
+def _csr():
+    g = inputs.grid(8, 8, 0, 0, seed=1, weights=(1, 9))
+    return g
+
+
+@pytest.mark.parametrize("case", ["n0", "rp0", "rpn", "decreasing", "col_range", "neg_w", "null_col", "null_out"])
+def test_graph_create_rejects_bad_csr_on_host(lib, case):
+    g = _csr()
+    n, m, rp, col, w = g.n, g.m, g.row_ptr.copy(), g.col.copy(), g.w.copy()
+    if case == "n0":
+        n = 0
+    elif case == "rp0":
+        rp[0] = 1
+    elif case == "rpn":
+        rp[-1] = m - 1
+    elif case == "decreasing":
+        rp[5] = rp[6] + 1
+    elif case == "col_range":
+        col[3] = n
+    elif case == "neg_w":
+        w[7] = -1
+    elif case == "null_col":
+        col = None
+    if case == "null_out":
+        st = lib.fg_graph_create(n, m, rp.ctypes.data, col.ctypes.data, w.ctypes.data, 0, None)
+    else:
+        st, h = fg.fg_graph_create(n, m, rp, col, w)
+        assert h is None
+    assert st == fg.FG_ERR_INVALID_ARG
+    assert fg.fg_last_error()
+
+
+def test_graph_create_rejects_huge_m(lib):
+    rp = np.zeros(2, dtype=np.int64)
+    st, _ = fg.fg_graph_create(1, 1 << 32, rp, rp)
+    assert st == fg.FG_ERR_UNSUPPORTED
+
+
+def test_batch_rejects_null_graph(lib):
+    src = np.zeros(4, dtype=np.int32)
+    out = np.zeros(16, dtype=np.uint32)
+    assert fg.fg_sssp_batch(None, src, 4, out) == fg.FG_ERR_INVALID_ARG
+    assert fg.fg_bfs_batch(None, src, 4, out) == fg.FG_ERR_INVALID_ARG
+    assert fg.fg_ppr_batch(None, src, 4, 0.15, 1e-4, out) == fg.FG_ERR_INVALID_ARG
+    st, _ = fg.fg_graph_info(None)
+    assert st == fg.FG_ERR_INVALID_ARG
+    assert fg.fg_graph_destroy(None) == fg.FG_OK
+
+
+def test_bad_graph_opts(lib):
+    g = _csr()
+    for method, S in ((7, 0), (fg.FG_PART_GROW, 100), (fg.FG_PART_GROW, 16), (fg.FG_PART_GROW, 8192)):
+        go = fg.fg_default_graph_opts(partition_method=method, partition_vertices=S)
+        st, _ = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, go)
+        assert st == fg.FG_ERR_INVALID_ARG
+
+
+def _cut(g, perm, S):
+    part = np.empty(g.n, dtype=np.int64)
+    part[perm] = np.arange(g.n) // S
+    src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    return int((part[src] != part[g.col]).sum())
+
+
+@pytest.mark.parametrize("S", [64, 1024])
+def test_partition_plan_is_a_permutation_with_compact_regions(lib, S):
+    g = inputs.grid(256, 256, 500, 100, seed=4)
+    perm = np.empty(g.n, dtype=np.int32)
+    assert fg.fg_partition_plan(g.n, g.row_ptr, g.col, fg.FG_PART_GROW, S, perm) == fg.FG_OK
+    assert np.array_equal(np.sort(perm), np.arange(g.n))
+    for j in range(0, g.n, S):  # ascending original ids inside a partition
+        assert np.all(np.diff(perm[j:j + S]) > 0)
+    rng = np.empty(g.n, dtype=np.int32)
+    assert fg.fg_partition_plan(g.n, g.row_ptr, g.col, fg.FG_PART_RANGE, S, rng) == fg.FG_OK
+    assert np.array_equal(rng, np.arange(g.n))
+    grow_cut, range_cut = _cut(g, perm, S), _cut(g, rng, S)
+    assert grow_cut < 0.6 * range_cut, (grow_cut, range_cut)
+
+
+def test_partition_plan_bad_args(lib):
+    perm = np.empty(4, dtype=np.int32)
+    assert fg.fg_partition_plan(4, None, None, fg.FG_PART_GROW, 2, perm) == fg.FG_ERR_INVALID_ARG
+    assert fg.fg_partition_plan(4, None, None, 9, 2, perm) == fg.FG_ERR_INVALID_ARG
