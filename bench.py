@@ -1,0 +1,374 @@
+#!/usr/bin/env python3
+"""Benchmark: batched BFS + SSSP source queries on a road-like 1024x1024 grid.
+
+One step = one fg_bfs_batch and one fg_sssp_batch over the same 1,024 seeded
+sources (2,048 source queries), followed by fg_sync. Three seeded source sets
+rotate across steps. Prints ONE JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fg|reference]
+
+Under torchrun (N > 1) every rank runs its own 1,024-source batches on its own
+GPU (weak scaling; queries are independent, so nothing is exchanged), and the
+slowest rank's time sets the whole-job rate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+WORKLOAD = "grid1024_bfs_sssp"
+GRAPH_DESC = ("road-like 2D grid 1024x1024 (1,048,576 vertices), 4-neighbour edges with 5% dropped, "
+              "1% diagonal shortcuts, int32 weights uniform in [100,10000]")
+NQ = 1024
+METRIC = "source-queries/s"
+UNIT = "queries/s"
+SOURCE_SETS = 3
+# Scheduling for this workload (per-query priority windows, i.e. Delta-stepping
+# across partitions; chosen by the sweep recorded in the design notes)
+TUNED_BFS = {"sched": 1, "sched_window": 16}
+TUNED_SSSP = {"sched": 1, "sched_window": 50000}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fg", choices=["fg", "reference"])
+    ap.add_argument("--nq", type=int, default=NQ, help="sources per batch (1,024 for the workload)")
+    ap.add_argument("--opts-bfs", default="", help="JSON overrides of fg_opts for the BFS batches")
+    ap.add_argument("--opts-sssp", default="", help="JSON overrides of fg_opts for the SSSP batches")
+    ap.add_argument("--partition-vertices", type=int, default=0)
+    ap.add_argument("--no-extras", action="store_true", help="skip the cpu/plain/e2e legs (profiling runs)")
+    ap.add_argument("--cpu-sample", type=int, default=512)
+    ap.add_argument("--plain-sample", type=int, default=8)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def source_sets(g, rank, nq=NQ):
+    from paper_2103_14915_gb300 import inputs
+    return [inputs.workload_sources(WORKLOAD, g, NQ, set_index=100 * rank + i)[:nq] for i in range(SOURCE_SETS)]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def engine_traffic():
+    """DRAM bytes per engine launch from the committed ncu summary, if it matches the kernel source."""
+    src = (ROOT / "paper_2103_14915_gb300" / "csrc" / "fg_engine.cu").read_bytes()
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    f = ROOT / "profiles" / "engine_grid1024_traffic.txt"
+    if not f.exists():
+        return None
+    kv = {}
+    for ln in f.read_text().splitlines():
+        if ":" in ln:
+            k, v = ln.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("engine_source_sha256_16") != sha:
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def run_reference(args):
+    """The oracle (CPU, OpenMP over queries) on a bounded sample of the same workload."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2103_14915_gb300 import inputs
+    g = inputs.workload_graph(WORKLOAD)
+    sets = source_sets(g, 0)
+    per_step = 32
+    cores = oracle.num_threads()
+    for i in range(args.warmup):
+        s = sets[i % SOURCE_SETS][:per_step]
+        oracle.bfs(g, s)
+        oracle.sssp(g, s)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        s = sets[i % SOURCE_SETS][:per_step]
+        oracle.bfs(g, s)
+        oracle.sssp(g, s)
+    dt = time.perf_counter() - t0
+    value = 2 * per_step * args.steps / dt
+    sample = f"{per_step} sources per step (BFS + SSSP each), {args.steps} steps"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "graph": GRAPH_DESC, "queries_per_step": 2 * per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if ws > 1:
+        dist.barrier()
+        __graft_entry__.build()
+    from paper_2103_14915_gb300 import fg, inputs
+
+    g = inputs.workload_graph(WORKLOAD)
+    nq = args.nq
+    sets = source_sets(g, rank, nq)
+    gopts = fg.fg_default_graph_opts(partition_method=fg.FG_PART_GROW, partition_vertices=args.partition_vertices)
+    st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, gopts)
+    fg.check(st)
+    st, info = fg.fg_graph_info(h)
+    fg.check(st)
+    extra_b = dict(TUNED_BFS, **(json.loads(args.opts_bfs) if args.opts_bfs else {}))
+    extra_s = dict(TUNED_SSSP, **(json.loads(args.opts_sssp) if args.opts_sssp else {}))
+    opts_b = fg.fg_default_opts(**extra_b)
+    opts_s = fg.fg_default_opts(**extra_s)
+    stream = torch.cuda.current_stream(dev)
+    src_d = [torch.from_numpy(s).to(dev) for s in sets]
+    level = torch.empty((nq, g.n), dtype=torch.int32, device=dev)
+    dist_t = torch.empty((nq, g.n), dtype=torch.int32, device=dev)
+
+    def step(i, ev=None):
+        s = src_d[i % SOURCE_SETS]
+        if ev is not None:
+            ev[0].record(stream)
+        fg.check(fg.fg_bfs_batch(h, s, nq, level, stream, opts_b))
+        if ev is not None:
+            ev[1].record(stream)
+        fg.check(fg.fg_sssp_batch(h, s, nq, dist_t, stream, opts_s))
+        if ev is not None:
+            ev[2].record(stream)
+        fg.check(fg.fg_sync(stream))
+
+    for i in range(args.warmup):
+        step(i)
+    # kernel launches per batch, from the library's own count
+    fg.check(fg.fg_bfs_batch(h, src_d[0], nq, level, stream, opts_b))
+    fg.check(fg.fg_sync(stream))
+    st, sb = fg.fg_stats(h)
+    fg.check(fg.fg_sssp_batch(h, src_d[0], nq, dist_t, stream, opts_s))
+    fg.check(fg.fg_sync(stream))
+    st, ss = fg.fg_stats(h)
+    launches_per_step = int(sb.launches + ss.launches)
+
+    clocks = ClockSampler(local)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    t_start.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i, evs[i])
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    if ws > 1:
+        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        elapsed_ms = float(t.item())
+    queries = 2 * nq * args.steps * ws
+    value = queries / (elapsed_ms / 1000.0)
+    bfs_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    sssp_ms = [e[1].elapsed_time(e[2]) for e in evs]
+
+    # GTEPS: arcs out of reachable vertices (the edges a sequential Dijkstra / BFS scans)
+    deg = torch.from_numpy(np.diff(g.row_ptr).astype(np.int64)).to(dev)
+    arcs_per_set = []
+    for i in range(SOURCE_SETS):
+        fg.check(fg.fg_bfs_batch(h, src_d[i], nq, level, stream, opts_b))
+        fg.check(fg.fg_sync(stream))
+        reach = level.view(torch.int32) != -1
+        arcs_per_set.append(int((reach.to(torch.int64) * deg[None, :]).sum().item()))
+    arcs = sum(2 * arcs_per_set[(args.warmup + i) % SOURCE_SETS] for i in range(args.steps)) * ws
+    gteps = arcs / (elapsed_ms / 1000.0) / 1e9
+
+    peak, peak_kind = measured_peaks()
+    graph_bytes = int(info.device_bytes)
+    alg_bytes = 4 * nq * g.n + graph_bytes  # dense output written once + graph read once per launch
+    kern_ms = statistics.mean(bfs_ms + sssp_ms)
+    achieved = alg_bytes / (kern_ms / 1000.0) / 1e9
+    traffic = engine_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": f"{peak_kind} hbm_gbs (STREAM-style copy)",
+                "kernel": "fg::engine_kernel", "algorithmic_bytes_per_launch": alg_bytes,
+                "kernel_ms": {"bfs": statistics.mean(bfs_ms), "sssp": statistics.mean(sssp_ms)}}
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "graph": GRAPH_DESC, "sources_per_batch": nq, "kinds": ["bfs", "sssp"],
+                   "queries_per_step": 2 * nq, "source_sets": SOURCE_SETS,
+                   "partition": {"method": "grow", "S": int(info.partition_vertices),
+                                 "parts": int(info.num_partitions), "cut_arcs": int(info.cut_arcs)},
+                   "opts": {"bfs": extra_b, "sssp": extra_s},
+                   "l2": f"inputs larger than L2: each step writes {8 * nq * g.n / 1e9:.1f} GB of query state",
+                   "parallelism": f"queries sharded over {ws} GPU(s)"},
+        "gteps": gteps,
+        "roofline": roofline,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "stats": {"bfs": {k: int(getattr(sb, k)) for k, _ in sb._fields_},
+                  "sssp": {k: int(getattr(ss, k)) for k, _ in ss._fields_}},
+    }
+
+    if not args.no_extras:
+        # end to end through the C ABI with host buffers (host_io): sources copied in, results copied out
+        import ctypes
+        o_hb = fg.fg_default_opts(**extra_b)
+        o_hb.host_io = 1
+        o_hs = fg.fg_default_opts(**extra_s)
+        o_hs.host_io = 1
+        lv_h = torch.empty((nq, g.n), dtype=torch.int32, pin_memory=True)
+        ds_h = torch.empty((nq, g.n), dtype=torch.int32, pin_memory=True)
+        src_h = [torch.from_numpy(s).pin_memory() for s in sets]
+        e_steps = max(1, min(args.steps, 4))
+        fg.check(fg.fg_bfs_batch(h, src_h[0].data_ptr(), nq, lv_h.data_ptr(), stream, o_hb))
+        fg.check(fg.fg_sync(stream))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for i in range(e_steps):
+            s = src_h[i % SOURCE_SETS].data_ptr()
+            fg.check(fg.fg_bfs_batch(h, s, nq, lv_h.data_ptr(), stream, o_hb))
+            fg.check(fg.fg_sssp_batch(h, s, nq, ds_h.data_ptr(), stream, o_hs))
+            fg.check(fg.fg_sync(stream))
+        e_dt = time.perf_counter() - t0
+        result["e2e"] = {"value": 2 * nq * e_steps / e_dt, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * nq,
+                         "d2h_bytes_per_step": 2 * 4 * nq * g.n, "steps": e_steps,
+                         "api": "fg_bfs_batch + fg_sssp_batch with host_io=1 (pinned host buffers)"}
+        del lv_h, ds_h
+        if rank == 0:
+            # plain per-query GPU form on a sample of the same sources
+            o_plain = fg.fg_default_opts(mode=fg.FG_MODE_PLAIN)
+            k = args.plain_sample
+            s = src_d[0][:k].contiguous()
+            fg.check(fg.fg_bfs_batch(h, s, 1, level, stream, o_plain))
+            fg.check(fg.fg_sync(stream))
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fg.check(fg.fg_bfs_batch(h, s, k, level, stream, o_plain))
+            fg.check(fg.fg_sssp_batch(h, s, k, dist_t, stream, o_plain))
+            b.record(stream)
+            fg.check(fg.fg_sync(stream))
+            pms = a.elapsed_time(b)
+            result["plain_gpu"] = {"value": 2 * k / (pms / 1000.0), "unit": UNIT,
+                                   "sample": f"{k} sources, BFS + SSSP, one query at a time (FG_MODE_PLAIN)"}
+            # CPU oracle on the host cores
+            import oracle
+            cs = source_sets(g, rank)[0][: args.cpu_sample]
+            t0 = time.perf_counter()
+            oracle.bfs(g, cs)
+            oracle.sssp(g, cs)
+            cdt = time.perf_counter() - t0
+            result["cpu_baseline"] = {"value": 2 * len(cs) / cdt, "unit": UNIT, "cores": oracle.num_threads(),
+                                      "kind": "oracle",
+                                      "sample": f"{len(cs)} of the 1,024 sources, BFS + SSSP, OpenMP over queries"}
+    fg.fg_graph_destroy(h)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -91,6 +91,9 @@ typedef struct {
     int32_t host_io;        /* 1: src and outputs are HOST pointers; the call copies them and
                                completes before returning (fg_sync still reports status) */
     int32_t query_batch;    /* queries per device launch; 0 = all (bounded by workspace) */
+    int32_t threads_per_vertex; /* SSSP/BFS expansion: 1 = one lane per frontier vertex (graphs
+                               with out-degree <= 8 only), 32 or 0 (default) = a warp shares
+                               a batch of 32 frontier vertices' arcs evenly */
 } fg_opts;
 
 /* counters of the last completed batch on a graph (read by fg_stats after fg_sync) */

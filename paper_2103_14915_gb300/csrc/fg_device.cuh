@@ -26,9 +26,17 @@ __device__ __forceinline__ int ld_volatile_i32(const int *p) {
 }
 
 // Raise a device status (first one wins) and ask every block to leave.
-__device__ __forceinline__ void raise_status(Ctrl *c, int status) {
-  atomicCAS(&c->status, 0, status);
+__device__ __forceinline__ void raise_status(Ctrl *c, int status, unsigned site = kSiteNone) {
+  if (atomicCAS(&c->status, 0, status) == 0) atomicExch(&c->site, site);
   atomicExch(&c->abort, 1);
+}
+
+// Block barrier that first reconverges the calling warp: __syncthreads() is an
+// aligned barrier and must be reached by whole, converged warps (a lane still
+// inside a thread-0-only region must not let its warp count as arrived).
+__device__ __forceinline__ void block_sync() {
+  __syncwarp();
+  __syncthreads();
 }
 
 // Device-wide barrier for a cooperative (co-resident) grid. Returns false if
@@ -36,7 +44,7 @@ __device__ __forceinline__ void raise_status(Ctrl *c, int status) {
 // longer than watchdog_ns and raised FG_ERR_TIMEOUT). Every spin is bounded.
 __device__ __forceinline__ bool grid_barrier(Ctrl *c, unsigned &gen, uint64_t watchdog_ns) {
   __shared__ int s_ok;
-  __syncthreads();
+  block_sync();
   if (threadIdx.x == 0) {
     int ok = 1;
     const unsigned my_gen = gen;
@@ -52,7 +60,7 @@ __device__ __forceinline__ bool grid_barrier(Ctrl *c, unsigned &gen, uint64_t wa
       while (ld_acquire_u32(&c->bar_gen) == my_gen) {
         if (ld_volatile_i32(&c->abort)) { ok = 0; break; }
         if ((++spins & 63u) == 0 && global_ns() - t0 > watchdog_ns) {
-          raise_status(c, FG_ERR_TIMEOUT);
+          raise_status(c, FG_ERR_TIMEOUT, kSiteBarrier);
           ok = 0;
           break;
         }
@@ -63,7 +71,7 @@ __device__ __forceinline__ bool grid_barrier(Ctrl *c, unsigned &gen, uint64_t wa
     if (ld_volatile_i32(&c->abort)) ok = 0;
     s_ok = ok;
   }
-  __syncthreads();
+  block_sync();
   gen += 1u;
   return s_ok != 0;
 }
@@ -107,6 +115,20 @@ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < 
 __device__ __forceinline__ uint32_t sat_add_u32(uint32_t a, uint32_t b) {
   uint32_t s = a + b;
   return s < a ? kInf : s;
+}
+
+}  // namespace fg
+
+namespace fg {
+
+// ---- 16-byte asynchronous global -> shared copies (cp.async, L2 only) ----
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
 
 }  // namespace fg

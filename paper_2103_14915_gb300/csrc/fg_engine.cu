@@ -33,7 +33,9 @@ namespace fg {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr uint32_t kMaxVisitSteps = 1u << 22;  // relax/push steps of one visit before the watchdog fires
+constexpr uint32_t kMaxVisitSteps = 1u << 22;
+constexpr uint32_t kWarpClaim = 2;              // work items a warp claims at once
+constexpr int kLaneMaxDeg = 8;                   // lane-per-vertex expansion for max out-degree <= 8  // relax/push steps of one visit before the watchdog fires
 
 // Per-warp counters. visits and edges are lane-uniform; spills and yields are
 // summed over the lanes when flushed.
@@ -52,6 +54,7 @@ struct WarpSmem {
 };
 
 __host__ __device__ inline size_t warp_smem_words(int S) { return (size_t)S + 5u * (size_t)(S / 32); }
+
 
 // ---------------------------------------------------------------------------
 // Warp-collective append of at most one operation per lane to the arena.
@@ -142,11 +145,58 @@ __device__ __forceinline__ uint32_t slice_index(const DevGraph &g, uint32_t inte
   return g.orig ? (uint32_t)g.orig[internal] : internal;
 }
 
+// CSR view of the resident partition. rp is indexed by the local vertex id and
+// holds absolute arc offsets; adj / wt are indexed by (arc - off).
+struct PartView {
+  const uint32_t *rp;
+  const uint32_t *adj;
+  const uint32_t *wt;
+  uint32_t off;
+  uint32_t narc;  // arcs addressable through adj/wt: [off, off + narc)
+  uint32_t part;  // partition this view belongs to
+};
+
+// A vertex's arc range must lie inside the view (never index outside it).
+__device__ __forceinline__ bool arcs_in_view(const PartView &pv, uint32_t e0, uint32_t deg) {
+  return e0 >= pv.off && (uint64_t)(e0 - pv.off) + deg <= (uint64_t)pv.narc;
+}
+
+__device__ __forceinline__ uint32_t relax_value(const EngineArgs &a, uint32_t d, uint32_t w) {
+  const uint64_t s64 = (uint64_t)d + (uint64_t)w;
+  if (s64 >= (uint64_t)kInf) {
+    atomicCAS(&a.ctrl->status, 0, (int)FG_ERR_OVERFLOW);
+    return kInf - 1u;
+  }
+  return (uint32_t)s64;
+}
+
+// Lower a partition-local vertex and route it: next step (< T), far window
+// ([T, Ty)) or a later visit (>= Ty), clearing the bit of its previous class.
+__device__ __forceinline__ void relax_local(const WarpSmem &w, uint32_t lu, uint32_t nd, uint32_t T, uint32_t Ty) {
+  const uint32_t bit = 1u << (lu & 31);
+  const uint32_t old = atomicMin(&w.d[lu], nd);
+  if (nd < old) {
+    if (nd < T) {
+      atomicOr(&w.nxt[lu >> 5], bit);
+      if (old != kInf && old >= T) {
+        if (old < Ty) atomicAnd(&w.far[lu >> 5], ~bit);
+        else atomicAnd(&w.carry[lu >> 5], ~bit);
+      }
+    } else if (nd < Ty) {
+      atomicOr(&w.far[lu >> 5], bit);
+      if (old != kInf && old >= Ty) atomicAnd(&w.carry[lu >> 5], ~bit);
+    } else {
+      atomicOr(&w.carry[lu >> 5], bit);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // SSSP / BFS visit of one (partition, query) buffer.
 // ---------------------------------------------------------------------------
-template <int QT>
-__device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, Counters &ctr) {
+template <int QT, bool LANES>
+__device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, uint32_t qbound, const PartView &pv,
+                           Counters &ctr) {
   const DevGraph &g = a.g;
   const int lane = lane_id();
   const uint32_t key = item.x, off = item.y, cnt = item.z, flags = item.w;
@@ -158,6 +208,10 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
   uint32_t *drow = a.dist + (size_t)q * (size_t)g.n;
   WarpSmem w = w0;
   const WordRange wr(nw, lane);
+  if (pv.part != p) {  // the resident CSR must be this item's partition
+    if (lane == 0) raise_status(a.ctrl, FG_ERR_CUDA, kSiteStage);
+    return;
+  }
 
   // 1. stage the query's slice of this partition (bypassing L1)
   if (g.orig) {
@@ -181,7 +235,7 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
   // 3. apply buffered operations; an operation is live iff it improves the value
   const uint2 *ops = a.b_op + off;
   for (uint32_t j = lane; j < cnt; j += 32) {
-    const uint2 o = ops[j];
+    const uint2 o = __ldcg(ops + j);
     const uint32_t old = atomicMin(&w.d[o.x], o.y);
     if (o.y < old) atomicOr(&w.cur[o.x >> 5], 1u << (o.x & 31));
   }
@@ -200,7 +254,10 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
   fmin = warp_min_u32(fmin);
   if (fmin == kInf) return;  // every operation was stale: the slice is unchanged
   ctr.visits++;
-  const uint32_t Ty = a.delta ? sat_add_u32(fmin, a.delta) : kInf;
+  // values at or beyond Ty stay buffered for a later visit: the yield window
+  // (first value + delta) and, under priority scheduling, the query's round
+  // bound (best pending value + window), i.e. Delta-stepping across partitions
+  const uint32_t Ty = min(a.delta ? sat_add_u32(fmin, a.delta) : kInf, qbound);
   uint32_t T = a.bucket ? min(sat_add_u32(fmin, a.bucket), Ty) : Ty;
   if (T != kInf) {
     for (int wd = wr.w0; wd < wr.w1; ++wd) {
@@ -220,17 +277,21 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
   uint64_t vis_edges = 0;
   bool stopped = false;
   uint32_t steps = 0;
-  const uint32_t *__restrict__ rp = g.rp;
-  const uint32_t *__restrict__ adj = g.adj;
-  const uint32_t *__restrict__ wt = g.wt;
   for (;;) {
     // bounded loop: a visit can never spin forever
     if (++steps > kMaxVisitSteps || ((steps & 255u) == 0 && ld_volatile_i32(&a.ctrl->abort))) {
-      if (steps > kMaxVisitSteps) raise_status(a.ctrl, FG_ERR_TIMEOUT);
+      if (steps > kMaxVisitSteps) raise_status(a.ctrl, FG_ERR_TIMEOUT, kSiteVisit);
       stopped = true;
       break;
     }
-    const uint32_t F = frontier_prefix(w, wr);
+    uint32_t F;
+    if (LANES) {
+      uint32_t cntl = 0;
+      for (int wd = wr.w0; wd < wr.w1; ++wd) cntl += __popc(w.cur[wd]);
+      F = __reduce_add_sync(kFull, cntl);
+    } else {
+      F = frontier_prefix(w, wr);
+    }
     if (F == 0) {
       // advance the in-visit window to the smallest far value
       uint32_t fm = kInf;
@@ -262,69 +323,110 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
       stopped = true;
       break;
     }
-    for (uint32_t b0 = 0; b0 < F; b0 += 32) {
-      const uint32_t idx = b0 + (uint32_t)lane;
-      uint32_t v = 0, dv = 0, a0 = 0, deg = 0;
-      if (idx < F) {
-        v = frontier_select(w, nw, idx);
-        dv = w.d[v];
-        a0 = rp[base + v];
-        deg = rp[base + v + 1] - a0;
-      }
-      const uint32_t incl = warp_incl_scan(deg);
-      const uint32_t exd = incl - deg;
-      const uint32_t tot = __shfl_sync(kFull, incl, 31);
-      vis_edges += tot;
-      for (uint32_t j = 0; j < tot; j += 32) {
-        const uint32_t t = j + (uint32_t)lane;
-        const bool has = t < tot;
-        const int L = owner_lane(exd, has ? t : 0u);
-        const uint32_t eL = __shfl_sync(kFull, a0, L) + (t - __shfl_sync(kFull, exd, L));
-        const uint32_t du = __shfl_sync(kFull, dv, L);
-        const uint32_t vL = __shfl_sync(kFull, v, L);
-        uint32_t u = 0, nd = 0;
-        bool ext = false;
-        if (has) {
-          u = adj[eL];
-          const uint32_t wgt = (QT == Q_BFS || wt == nullptr) ? 1u : wt[eL];
-          const uint64_t s64 = (uint64_t)du + (uint64_t)wgt;
-          if (s64 >= (uint64_t)kInf) {
-            atomicCAS(&a.ctrl->status, 0, (int)FG_ERR_OVERFLOW);
-            nd = kInf - 1u;
-          } else {
-            nd = (uint32_t)s64;
+    if (LANES) {
+      // low-degree graphs: each lane expands the frontier vertices of its own
+      // bitmap words, loading all arcs of a vertex at once
+      const int per = (nw + 31) >> 5;
+      for (int k = 0; k < per; ++k) {
+        const int wd = wr.w0 + k;
+        uint32_t b = (wd < wr.w1) ? w.cur[wd] : 0u;
+        while (__any_sync(kFull, b != 0u)) {
+          uint32_t v = 0, dv = 0, e0 = 0, deg = 0;
+          if (b) {
+            const int t = __ffs(b) - 1;
+            b &= b - 1;
+            v = (uint32_t)wd * 32u + (uint32_t)t;
+            dv = w.d[v];
+            e0 = pv.rp[v];
+            deg = pv.rp[v + 1] - e0;
+            if (deg > (uint32_t)kLaneMaxDeg || !arcs_in_view(pv, e0, deg)) {  // inconsistent view: skip
+              raise_status(a.ctrl, FG_ERR_CUDA, kSiteDegree);
+              deg = 0;
+            }
           }
-          if ((u >> g.slog2) == p) {
-            const uint32_t lu = u & (uint32_t)(S - 1);
-            const uint32_t bit = 1u << (lu & 31);
-            const uint32_t old = atomicMin(&w.d[lu], nd);
-            if (nd < old) {
-              if (nd < T) {
-                atomicOr(&w.nxt[lu >> 5], bit);
-                if (old != kInf && old >= T) {
-                  if (old < Ty) atomicAnd(&w.far[lu >> 5], ~bit);
-                  else atomicAnd(&w.carry[lu >> 5], ~bit);
-                }
-              } else if (nd < Ty) {
-                atomicOr(&w.far[lu >> 5], bit);
-                if (old != kInf && old >= Ty) atomicAnd(&w.carry[lu >> 5], ~bit);
-              } else {
-                atomicOr(&w.carry[lu >> 5], bit);
+          vis_edges += __reduce_add_sync(kFull, deg);
+          uint32_t u[kLaneMaxDeg], nd[kLaneMaxDeg];
+#pragma unroll
+          for (int j = 0; j < kLaneMaxDeg; ++j) {
+            u[j] = 0u;
+            nd[j] = 0u;
+            if ((uint32_t)j < deg) {
+              u[j] = pv.adj[e0 - pv.off + j];
+              const uint32_t wgt = (QT == Q_BFS || pv.wt == nullptr) ? 1u : pv.wt[e0 - pv.off + j];
+              nd[j] = relax_value(a, dv, wgt);
+            }
+          }
+          uint32_t extm = 0u;
+#pragma unroll
+          for (int j = 0; j < kLaneMaxDeg; ++j) {
+            if ((uint32_t)j < deg) {
+              if ((u[j] >> g.slog2) == p) {
+                relax_local(w, u[j] & (uint32_t)(S - 1), nd[j], T, Ty);
+              } else if (nd[j] < a.dist[(size_t)q * (size_t)g.n + slice_index(g, u[j])]) {
+                extm |= 1u << j;
               }
             }
-          } else {
-            const uint32_t cur_g = a.dist[(size_t)q * (size_t)g.n + slice_index(g, u)];
-            ext = nd < cur_g;
           }
-        }
-        const uint32_t pk = (u >> g.slog2) * nq + q;
-        const bool ok = emit_ops(a, ext, pk, u & (uint32_t)(S - 1), nd, true);
-        if (!ok) {
-          atomicOr(&w.carry[vL >> 5], 1u << (vL & 31));
-          ctr.spills++;
+          if (__any_sync(kFull, extm != 0u)) {
+#pragma unroll
+            for (int j = 0; j < kLaneMaxDeg; ++j) {
+              const bool e = (extm >> j) & 1u;
+              const uint32_t pk = (u[j] >> g.slog2) * nq + q;
+              if (!emit_ops(a, e, pk, u[j] & (uint32_t)(S - 1), nd[j], true)) {
+                atomicOr(&w.carry[v >> 5], 1u << (v & 31));
+                ctr.spills++;
+              }
+            }
+          }
         }
       }
       __syncwarp();
+    } else {
+      // any degree distribution: the batch's arcs are spread evenly over the lanes
+      for (uint32_t b0 = 0; b0 < F; b0 += 32) {
+        const uint32_t idx = b0 + (uint32_t)lane;
+        uint32_t v = 0, dv = 0, a0 = 0, deg = 0;
+        if (idx < F) {
+          v = frontier_select(w, nw, idx);
+          dv = w.d[v];
+          a0 = pv.rp[v];
+          deg = pv.rp[v + 1] - a0;
+          if (deg > g.max_deg || !arcs_in_view(pv, a0, deg)) {  // inconsistent view: skip
+            raise_status(a.ctrl, FG_ERR_CUDA, kSiteDegree);
+            deg = 0;
+          }
+        }
+        const uint32_t incl = warp_incl_scan(deg);
+        const uint32_t exd = incl - deg;
+        const uint32_t tot = __shfl_sync(kFull, incl, 31);
+        vis_edges += tot;
+        for (uint32_t j = 0; j < tot; j += 32) {
+          const uint32_t t = j + (uint32_t)lane;
+          const bool has = t < tot;
+          const int L = owner_lane(exd, has ? t : 0u);
+          const uint32_t eL = __shfl_sync(kFull, a0, L) + (t - __shfl_sync(kFull, exd, L));
+          const uint32_t du = __shfl_sync(kFull, dv, L);
+          const uint32_t vL = __shfl_sync(kFull, v, L);
+          uint32_t u = 0, nd = 0;
+          bool ext = false;
+          if (has) {
+            u = pv.adj[eL - pv.off];
+            const uint32_t wgt = (QT == Q_BFS || pv.wt == nullptr) ? 1u : pv.wt[eL - pv.off];
+            nd = relax_value(a, du, wgt);
+            if ((u >> g.slog2) == p) {
+              relax_local(w, u & (uint32_t)(S - 1), nd, T, Ty);
+            } else {
+              ext = nd < a.dist[(size_t)q * (size_t)g.n + slice_index(g, u)];
+            }
+          }
+          const uint32_t pk = (u >> g.slog2) * nq + q;
+          if (!emit_ops(a, ext, pk, u & (uint32_t)(S - 1), nd, true)) {
+            atomicOr(&w.carry[vL >> 5], 1u << (vL & 31));
+            ctr.spills++;
+          }
+        }
+        __syncwarp();
+      }
     }
     // retire the expanded frontier; the next step expands nxt
     for (int wd = wr.w0; wd < wr.w1; ++wd) w.cur[wd] = 0u;
@@ -370,12 +472,13 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
 // Residuals of the slice live in shared memory; estimates and their Kahan
 // compensation are updated in global memory (single writer per slice).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float ppr_thr(const DevGraph &g, float eps, uint32_t v_internal) {
-  const uint32_t d = g.rp[v_internal + 1] - g.rp[v_internal];
+__device__ __forceinline__ float ppr_thr(const PartView &pv, float eps, uint32_t v_local) {
+  const uint32_t d = pv.rp[v_local + 1] - pv.rp[v_local];
   return eps * (float)(d > 0u ? d : 1u);
 }
 
-__device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, Counters &ctr) {
+
+__device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, const PartView &pv, Counters &ctr) {
   const DevGraph &g = a.g;
   const int lane = lane_id();
   const uint32_t key = item.x, off = item.y, cnt = item.z, flags = item.w;
@@ -394,6 +497,10 @@ __device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, C
   const float alpha = a.alpha, eps = a.eps;
   const float beta = 1.0f - alpha;
   const uint32_t src_int = g.intl ? (uint32_t)g.intl[a.src[q]] : (uint32_t)a.src[q];
+  if (pv.part != p) {  // the resident CSR must be this item's partition
+    if (lane == 0) raise_status(a.ctrl, FG_ERR_CUDA, kSiteStage);
+    return;
+  }
 
   for (int i = lane; i < Sp; i += 32) rs[i] = __ldcg(rrow + slice_index(g, base + i));
   for (int i = Sp + lane; i < S; i += 32) rs[i] = 0.f;
@@ -410,9 +517,9 @@ __device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, C
   __syncwarp();
   const uint2 *ops = a.b_op + off;
   for (uint32_t j = lane; j < cnt; j += 32) {
-    const uint2 o = ops[j];
+    const uint2 o = __ldcg(ops + j);
     const float inc = __uint_as_float(o.y);
-    const float thr = ppr_thr(g, eps, base + o.x);
+    const float thr = ppr_thr(pv, eps, o.x);
     const float old = atomicAdd(&rs[o.x], inc);
     if (old < thr && __fadd_rn(old, inc) >= thr) atomicOr(&w.cur[o.x >> 5], 1u << (o.x & 31));
   }
@@ -421,11 +528,9 @@ __device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, C
   uint64_t vis_edges = 0;
   bool stopped = false, touched = (cnt > 0) || (flags & 1u);
   uint32_t steps = 0;
-  const uint32_t *__restrict__ rp = g.rp;
-  const uint32_t *__restrict__ adj = g.adj;
   for (;;) {
     if (++steps > kMaxVisitSteps || ((steps & 255u) == 0 && ld_volatile_i32(&a.ctrl->abort))) {
-      if (steps > kMaxVisitSteps) raise_status(a.ctrl, FG_ERR_TIMEOUT);
+      if (steps > kMaxVisitSteps) raise_status(a.ctrl, FG_ERR_TIMEOUT, kSiteVisit);
       stopped = true;
       break;
     }
@@ -441,8 +546,12 @@ __device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, C
       uint32_t v = 0, a0 = 0, deg = 0;
       if (valid) {
         v = frontier_select(w, nw, idx);
-        a0 = rp[base + v];
-        deg = rp[base + v + 1] - a0;
+        a0 = pv.rp[v];
+        deg = pv.rp[v + 1] - a0;
+        if (deg > g.max_deg || !arcs_in_view(pv, a0, deg)) {  // inconsistent view: skip
+          raise_status(a.ctrl, FG_ERR_CUDA, kSiteDegree);
+          deg = 0;
+        }
       }
       // arcs this lane's vertex contributes (a dangling vertex sends one
       // operation back to the source)
@@ -460,7 +569,7 @@ __device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, C
         const uint32_t eL = __shfl_sync(kFull, a0, L) + (t - __shfl_sync(kFull, exd, L));
         bool ext = false;
         if (has) {
-          const uint32_t u = degL > 0u ? adj[eL] : src_int;
+          const uint32_t u = degL > 0u ? pv.adj[eL - pv.off] : src_int;
           ext = (u >> g.slog2) != p;
         }
         n_ext += __popc(__ballot_sync(kFull, ext));
@@ -470,7 +579,7 @@ __device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, C
       rbase = __shfl_sync(kFull, rbase, 0);
       if (n_ext && rbase + n_ext > a.e_cap) {
         // does not fit this round: keep these vertices for a later visit
-        if (n_ext > a.e_cap) raise_status(a.ctrl, FG_ERR_BIN_OVERFLOW);
+        if (n_ext > a.e_cap) raise_status(a.ctrl, FG_ERR_BIN_OVERFLOW, kSiteArena);
         for (unsigned long long s = rbase + lane; s < a.e_cap && s < rbase + n_ext; s += 32)
           a.e_key[s] = kInvalidKey;
         if (valid) atomicOr(&w.carry[v >> 5], 1u << (v & 31));
@@ -483,11 +592,11 @@ __device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, C
       if (valid) {
         rho = atomicExch(&rs[v], 0.f);
         const uint32_t gi = slice_index(g, base + v);
-        const float pv = prow[gi], cv = crow[gi];
-        const float y = __fsub_rn(__fmul_rn(alpha, rho), cv);
-        const float tsum = __fadd_rn(pv, y);
-        crow[gi] = __fsub_rn(__fsub_rn(tsum, pv), y);
-        prow[gi] = tsum;
+        const float pe = __ldcg(prow + gi), ce = __ldcg(crow + gi);
+        const float y = __fsub_rn(__fmul_rn(alpha, rho), ce);
+        const float tsum = __fadd_rn(pe, y);
+        __stcg(crow + gi, __fsub_rn(__fsub_rn(tsum, pe), y));
+        __stcg(prow + gi, tsum);
         inc_l = deg > 0u ? __fdiv_rn(__fmul_rn(beta, rho), (float)deg) : __fmul_rn(beta, rho);
       }
       vis_edges += tot;
@@ -503,10 +612,10 @@ __device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, C
         bool ext = false;
         uint32_t u = 0;
         if (has) {
-          u = degL > 0u ? adj[eL] : src_int;
+          u = degL > 0u ? pv.adj[eL - pv.off] : src_int;
           if ((u >> g.slog2) == p) {
             const uint32_t lu = u & (uint32_t)(S - 1);
-            const float thr = ppr_thr(g, eps, u);
+            const float thr = ppr_thr(pv, eps, lu);
             const float old = atomicAdd(&rs[lu], inc);
             if (old < thr && __fadd_rn(old, inc) >= thr) atomicOr(&w.nxt[lu >> 5], 1u << (lu & 31));
           } else {
@@ -566,7 +675,7 @@ __device__ void carry_item(const EngineArgs &a, uint4 item, uint32_t item_prio) 
   uint32_t *pend = a.pend + (size_t)key * (size_t)nw;
   bool any = false;
   for (uint32_t j = lane; j < cnt; j += 32) {
-    const uint2 o = a.b_op[off + j];
+    const uint2 o = __ldcg(a.b_op + off + j);
     const uint32_t old = atomicMin(drow + slice_index(g, base + o.x), o.y);
     if (o.y < old) {
       atomicOr(pend + (o.x >> 5), 1u << (o.x & 31));
@@ -588,23 +697,23 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
   const int lane = lane_id(), wid = threadIdx.x >> 5;
   const unsigned long long incl = warp_incl_scan(x);
   if (lane == 31) s_warp[wid] = incl;
-  __syncthreads();
+  block_sync();
   if (wid == 0) {
     unsigned long long v = lane < kWarps ? s_warp[lane] : 0ull;
     const unsigned long long vi = warp_incl_scan(v);
     if (lane < kWarps) s_warp[lane] = vi - v;
     if (lane == kWarps - 1) s_warp[kWarps] = vi;
   }
-  __syncthreads();
+  block_sync();
   const unsigned long long ex = s_warp[wid] + incl - x;
   total = s_warp[kWarps];
-  __syncthreads();
+  block_sync();
   return ex;
 }
 
 template <int QT>
-__global__ void __launch_bounds__(kThreads) engine_kernel(EngineArgs a) {
-  extern __shared__ uint32_t smem_dyn[];
+__global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
+  extern __shared__ __align__(16) uint32_t smem_dyn[];
   __shared__ unsigned long long s_scan[kWarps + 1];
   __shared__ unsigned long long s_pre[2];
   constexpr bool kPPR = (QT == Q_PPR);
@@ -642,7 +751,7 @@ __global__ void __launch_bounds__(kThreads) engine_kernel(EngineArgs a) {
     } else {
       fill_u32(a.dist, rows, kInf, tid, nthr);
       fill_u32(a.prio, K, kInf, tid, nthr);
-      fill_u32(a.qbest, (uint64_t)a.nq, kInf, tid, nthr);
+      fill_u32(a.qbest, 2u * (uint64_t)a.nq, kInf, tid, nthr);
     }
     fill_u32(a.cnt, K, 0u, tid, nthr);
     fill_u32(a.dirty, K, 0u, tid, nthr);
@@ -655,7 +764,7 @@ __global__ void __launch_bounds__(kThreads) engine_kernel(EngineArgs a) {
     bool has = q < (uint32_t)a.nq;
     uint32_t key = 0, lv = 0;
     if (has && (a.src[q] < 0 || a.src[q] >= a.g.n)) {
-      raise_status(c, FG_ERR_INVALID_ARG);  // source id out of range
+      raise_status(c, FG_ERR_INVALID_ARG, kSiteSource);  // source id out of range
       has = false;
     }
     if (has) {
@@ -666,24 +775,28 @@ __global__ void __launch_bounds__(kThreads) engine_kernel(EngineArgs a) {
     }
     const uint32_t val0 = kPPR ? __float_as_uint(1.0f) : 0u;
     const bool ok = emit_ops(a, has, key, lv, val0, !kPPR);
-    if (!ok) raise_status(c, FG_ERR_BIN_OVERFLOW);
+    if (!ok) raise_status(c, FG_ERR_BIN_OVERFLOW, kSiteArena);
   }
   if (!grid_barrier(c, gen, a.watchdog_ns)) goto done;
 
   for (uint32_t round = 0;; ++round) {
+    // best pending value per query: written in SCAN-A, read in SCAN-B and PROCESS,
+    // and the other half is cleared in SCATTER for the next round
+    uint32_t *qb_cur = a.qbest + (size_t)(round & 1u) * (size_t)a.nq;
+    uint32_t *qb_nxt = a.qbest + (size_t)((round + 1u) & 1u) * (size_t)a.nq;
     // ---- SCAN-A: per-block totals ----
     {
       unsigned long long loc = 0;
       for (uint64_t k = k0 + threadIdx.x; k < k1; k += kThreads) {
-        const uint32_t n_ops = a.cnt[k];
-        const bool act = n_ops > 0u || a.dirty[k] != 0u;
+        const uint32_t n_ops = __ldcg(a.cnt + k);
+        const bool act = n_ops > 0u || __ldcg(a.dirty + k) != 0u;
         loc += ((unsigned long long)n_ops << 32) | (act ? 1ull : 0ull);
         if (!kPPR && act && a.sched == FG_SCHED_PRIORITY)
-          atomicMin(&a.qbest[k % (uint64_t)a.nq], a.prio[k]);
+          atomicMin(&qb_cur[k % (uint64_t)a.nq], __ldcg(a.prio + k));
       }
       loc = warp_sum(loc);
       if (lane == 0) s_scan[wid] = loc;
-      __syncthreads();
+      block_sync();
       if (threadIdx.x == 0) {
         unsigned long long t = 0;
         for (int i = 0; i < kWarps; ++i) t += s_scan[i];
@@ -696,37 +809,37 @@ __global__ void __launch_bounds__(kThreads) engine_kernel(EngineArgs a) {
     {
       unsigned long long pre = 0, all = 0;
       for (int i = threadIdx.x; i < (int)gridDim.x; i += kThreads) {
-        const unsigned long long v = a.blocksum[i];
+        const unsigned long long v = __ldcg(a.blocksum + i);
         all += v;
         if (i < (int)blockIdx.x) pre += v;
       }
       pre = warp_sum(pre);
       all = warp_sum(all);
       if (lane == 0) s_scan[wid] = pre;
-      __syncthreads();
+      block_sync();
       if (threadIdx.x == 0) {
         unsigned long long t = 0;
         for (int i = 0; i < kWarps; ++i) t += s_scan[i];
         s_pre[0] = t;
       }
-      __syncthreads();
+      block_sync();
       if (lane == 0) s_scan[wid] = all;
-      __syncthreads();
+      block_sync();
       if (threadIdx.x == 0) {
         unsigned long long t = 0;
         for (int i = 0; i < kWarps; ++i) t += s_scan[i];
         s_pre[1] = t;
       }
-      __syncthreads();
+      block_sync();
       pre = s_pre[0];
       all = s_pre[1];
       tot_ops = all >> 32;
       tot_items = all & 0xFFFFFFFFull;
       emitted = umin64(*reinterpret_cast<volatile unsigned long long *>(&c->e_cursor), a.e_cap);
-      __syncthreads();
+      block_sync();
       if (tot_items == 0) break;
       if (round >= a.max_rounds) {
-        if (threadIdx.x == 0) raise_status(c, FG_ERR_TIMEOUT);
+        if (threadIdx.x == 0) raise_status(c, FG_ERR_TIMEOUT, kSiteRounds);
         break;
       }
       unsigned long long run = pre;
@@ -736,8 +849,8 @@ __global__ void __launch_bounds__(kThreads) engine_kernel(EngineArgs a) {
         uint32_t n_ops = 0, dflag = 0, pr = kInf;
         bool act = false;
         if (k < k1) {
-          n_ops = a.cnt[k];
-          dflag = a.dirty[k];
+          n_ops = __ldcg(a.cnt + k);
+          dflag = __ldcg(a.dirty + k);
           act = n_ops > 0u || dflag != 0u;
         }
         const unsigned long long x = ((unsigned long long)n_ops << 32) | (act ? 1ull : 0ull);
@@ -748,9 +861,9 @@ __global__ void __launch_bounds__(kThreads) engine_kernel(EngineArgs a) {
           const uint32_t off = (uint32_t)(ex >> 32);
           uint32_t fl = dflag ? 1u : 0u;
           if (!kPPR) {
-            pr = a.prio[k];
+            pr = __ldcg(a.prio + k);
             if (a.sched == FG_SCHED_PRIORITY) {
-              const uint32_t qb = a.qbest[k % (uint64_t)a.nq];
+              const uint32_t qb = __ldcg(qb_cur + k % (uint64_t)a.nq);
               if (pr > sat_add_u32(qb, window)) fl |= 2u;
             }
             a.prio[k] = kInf;
@@ -778,7 +891,7 @@ __global__ void __launch_bounds__(kThreads) engine_kernel(EngineArgs a) {
       }
       if (!kPPR && a.sched == FG_SCHED_PRIORITY)
         for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < (uint32_t)a.nq; i += gridDim.x * kThreads)
-          a.qbest[i] = kInf;
+          qb_nxt[i] = kInf;
       const unsigned long long n_emit = emitted;
       for (unsigned long long i0 = (unsigned long long)gwarp * 32ull; i0 < n_emit; i0 += (unsigned long long)nwarps * 32ull) {
         const unsigned long long i = i0 + lane;
@@ -786,8 +899,8 @@ __global__ void __launch_bounds__(kThreads) engine_kernel(EngineArgs a) {
         uint32_t key = kInvalidKey;
         uint2 o = make_uint2(0u, 0u);
         if (has0) {
-          key = a.e_key[i];
-          o = a.e_op[i];
+          key = __ldcg(a.e_key + i);
+          o = __ldcg(a.e_op + i);
         }
         const bool has = has0 && key != kInvalidKey;
         const unsigned m = __ballot_sync(kFull, has);
@@ -804,20 +917,41 @@ __global__ void __launch_bounds__(kThreads) engine_kernel(EngineArgs a) {
     }
     if (!grid_barrier(c, gen, a.watchdog_ns)) goto done;
     // ---- PROCESS: IntraPartProcess of every work item ----
+    // Warps claim kWarpClaim consecutive items at a time (ordered by
+    // partition, then query, so one warp's items share the partition's CSR in
+    // L1). The resident partition lives in L2: the graph and the round's
+    // active state slices fit in it. No block-level synchronisation here.
     {
       for (;;) {
-        uint32_t idx = 0;
-        if (lane == 0) idx = atomicAdd(&c->item_next, 1u);
-        idx = __shfl_sync(kFull, idx, 0);
-        if (idx >= (uint32_t)tot_items) break;
-        if (ld_volatile_i32(&c->abort)) break;
-        const uint4 it = a.items[idx];
-        if (!kPPR && (it.w & 2u)) {
-          carry_item(a, it, a.iprio[idx]);
-        } else if (kPPR) {
-          visit_ppr(a, w, it, ctr);
-        } else {
-          visit_dist<QT>(a, w, it, ctr);
+        uint32_t i0 = 0;
+        if (lane == 0) {
+          i0 = atomicAdd(&c->item_next, kWarpClaim);
+          if (ld_volatile_i32(&c->abort)) i0 = 0xFFFFFFFFu;
+        }
+        i0 = __shfl_sync(kFull, i0, 0);
+        if (i0 >= (uint32_t)tot_items) break;
+        const uint32_t i1 = (uint32_t)umin64(tot_items, (uint64_t)i0 + kWarpClaim);
+        for (uint32_t idx = i0; idx < i1; ++idx) {
+          const uint4 it = __ldcg(a.items + idx);
+          const uint32_t p = it.x / (uint32_t)a.nq;
+          PartView pv;
+          pv.rp = a.g.rp + ((size_t)p << a.g.slog2);
+          pv.adj = a.g.adj;
+          pv.wt = a.g.wt;
+          pv.off = 0u;
+          pv.narc = (uint32_t)a.g.m;
+          pv.part = p;
+          if (!kPPR && (it.w & 2u)) {
+            carry_item(a, it, __ldcg(a.iprio + idx));
+          } else if (kPPR) {
+            visit_ppr(a, w, it, pv, ctr);
+          } else {
+            const uint32_t q = it.x - p * (uint32_t)a.nq;
+            const uint32_t qbound =
+                a.sched == FG_SCHED_PRIORITY ? sat_add_u32(__ldcg(qb_cur + q), a.sched_window) : kInf;
+            if (a.lanes) visit_dist<QT, true>(a, w, it, qbound, pv, ctr);
+            else visit_dist<QT, false>(a, w, it, qbound, pv, ctr);
+          }
         }
       }
     }
@@ -857,7 +991,7 @@ __global__ void __launch_bounds__(256) ppr_finalize_kernel(float *p, const float
   if (mass) {
     acc = warp_sum(acc);
     if (lane_id() == 0) s_red[threadIdx.x >> 5] = acc;
-    __syncthreads();
+    block_sync();
     if (threadIdx.x == 0) {
       double t = 0.0;
       for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += s_red[i];

@@ -14,6 +14,10 @@ enum QType : int { Q_SSSP = 0, Q_BFS = 1, Q_PPR = 2 };
 constexpr uint32_t kInf = 0xFFFFFFFFu;
 constexpr uint32_t kInvalidKey = 0xFFFFFFFFu;
 
+// where a device status was raised (reported by fg_sync)
+enum : unsigned { kSiteNone = 0, kSiteBarrier = 1, kSiteStage = 2, kSiteVisit = 3, kSiteRounds = 4,
+                  kSiteSource = 5, kSiteArena = 6, kSiteDegree = 7 };
+
 // Graph in partition-major ("internal") vertex order. Partition j holds the
 // internal ids [j*S, (j+1)*S); S = 1 << slog2.
 struct DevGraph {
@@ -22,6 +26,7 @@ struct DevGraph {
   int32_t S = 0;
   int32_t nparts = 0;
   uint64_t m = 0;
+  uint32_t max_deg = 0;            // largest out-degree (bounds every arc loop)
   const uint32_t *rp = nullptr;    // [n+1] arc offsets
   const uint32_t *adj = nullptr;   // [m] internal target ids
   const uint32_t *wt = nullptr;    // [m] weights, or null (unit)
@@ -36,7 +41,7 @@ struct Ctrl {
   int status;                 // fg_status raised on the device (0 = ok)
   int abort;                  // set with status: every block leaves at its next check
   unsigned int item_next;     // work-claiming counter of the current round
-  unsigned int pad0;
+  unsigned int site;          // where the first status was raised (kSite*)
   unsigned long long e_cursor;  // operations reserved in the arena this round
   unsigned long long rounds, visits, edges, ops, spills, yields, max_round_ops;
 };
@@ -73,6 +78,7 @@ struct EngineArgs {
   uint64_t yield_edges = 0;
   uint32_t max_rounds = 0;
   uint64_t watchdog_ns = 0;
+  uint32_t lanes = 0;  // 1: lane-per-vertex expansion (max out-degree <= 8)
 };
 
 struct PlainArgs {

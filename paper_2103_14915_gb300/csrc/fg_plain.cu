@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs a) {
   }
   if (!grid_barrier(c, gen, a.watchdog_ns)) return;
   if (tid == 0) {
-    if (!src_ok) raise_status(c, FG_ERR_INVALID_ARG);
+    if (!src_ok) raise_status(c, FG_ERR_INVALID_ARG, kSiteSource);
     a.sizes[0] = 0u; a.sizes[1] = 0u; a.sizes[2] = 0u;
     if (kPPR) {
       a.rr[s] = 1.0f;
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs a) {
     uint32_t *nsize = &a.sizes[(it + 1u) % 3u];
     if (nF == 0u) break;
     if (it >= a.max_rounds) {
-      if (tid == 0) raise_status(c, FG_ERR_TIMEOUT);
+      if (tid == 0) raise_status(c, FG_ERR_TIMEOUT, kSiteRounds);
       break;
     }
     if (tid == 0) a.sizes[(it + 2u) % 3u] = 0u;
@@ -77,16 +77,16 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs a) {
       uint32_t v = 0, a0 = 0, deg = 0, dv = 0;
       float inc_l = 0.f;
       if (valid) {
-        v = F[idx];
+        v = __ldcg(F + idx);
         a0 = g.rp[v];
         deg = g.rp[v + 1] - a0;
         if (kPPR) {
           const float rho = atomicExch(&a.rr[v], 0.f);
-          const float pv = a.pp[v], cv = a.cc[v];
+          const float pv = __ldcg(a.pp + v), cv = __ldcg(a.cc + v);
           const float y = __fsub_rn(__fmul_rn(alpha, rho), cv);
           const float t = __fadd_rn(pv, y);
-          a.cc[v] = __fsub_rn(__fsub_rn(t, pv), y);
-          a.pp[v] = t;
+          __stcg(a.cc + v, __fsub_rn(__fsub_rn(t, pv), y));
+          __stcg(a.pp + v, t);
           inc_l = deg ? __fdiv_rn(__fmul_rn(beta, rho), (float)deg) : __fmul_rn(beta, rho);
         } else {
           dv = __ldcg(&a.dist[v]);
@@ -139,11 +139,11 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs a) {
   for (uint32_t i = tid; i < n; i += nthr) {
     const uint32_t gi = g.orig ? (uint32_t)g.orig[i] : i;
     if (kPPR) {
-      a.out_p[gi] = a.pp[i];
-      a.out_r[gi] = a.rr[i];
-      a.out_c[gi] = a.cc[i];
+      a.out_p[gi] = __ldcg(a.pp + i);
+      a.out_r[gi] = __ldcg(a.rr + i);
+      a.out_c[gi] = __ldcg(a.cc + i);
     } else {
-      a.out_u32[gi] = a.dist[i];
+      a.out_u32[gi] = __ldcg(a.dist + i);
     }
   }
   edges = warp_sum(edges);

@@ -119,6 +119,7 @@ struct fg_graph {
   int engine_blocks = 0, engine_threads = 0;
   size_t engine_smem = 0;
   int engine_qtype = -1;
+  uint32_t max_degree = 0;
   int plain_blocks = 0, plain_threads = 0;
 };
 
@@ -318,16 +319,23 @@ extern "C" fg_status fg_graph_create_ex(int64_t n, int64_t m, const int64_t *row
       return cleanup(fail(e_ == cudaErrorMemoryAllocation ? FG_ERR_OOM : FG_ERR_CUDA, "%s: %s", #expr, \
                           cudaGetErrorString(e_)));                                           \
   } while (0)
-  CUDA_TRY_G(g->rp.reserve(sizeof(uint32_t) * (size_t)(n + 1)));
-  CUDA_TRY_G(g->adj.reserve(sizeof(uint32_t) * (size_t)std::max<int64_t>(m, 1)));
+  // a partition's row offsets are read as rp[base, base + S] (S + 1 entries), so
+  // rp is padded to whole partitions; adj / wt get a small tail pad
+  const size_t rp_elems = (size_t)g->nparts * (size_t)S + 64, arc_elems = (size_t)m + 64;
+  CUDA_TRY_G(g->rp.reserve(sizeof(uint32_t) * rp_elems));
+  CUDA_TRY_G(g->adj.reserve(sizeof(uint32_t) * arc_elems));
+  CUDA_TRY_G(cudaMemset(g->rp.p, 0, sizeof(uint32_t) * rp_elems));
+  CUDA_TRY_G(cudaMemset(g->adj.p, 0, sizeof(uint32_t) * arc_elems));
   CUDA_TRY_G(cudaMemcpy(g->rp.p, i_rp.data(), sizeof(uint32_t) * (size_t)(n + 1), cudaMemcpyHostToDevice));
   if (m > 0) CUDA_TRY_G(cudaMemcpy(g->adj.p, i_adj.data(), sizeof(uint32_t) * (size_t)m, cudaMemcpyHostToDevice));
   g->graph_bytes = sizeof(uint32_t) * (size_t)(n + 1 + m);
   if (wt) {
-    CUDA_TRY_G(g->wt.reserve(sizeof(uint32_t) * (size_t)std::max<int64_t>(m, 1)));
+    CUDA_TRY_G(g->wt.reserve(sizeof(uint32_t) * arc_elems));
+    CUDA_TRY_G(cudaMemset(g->wt.p, 0, sizeof(uint32_t) * arc_elems));
     if (m > 0) CUDA_TRY_G(cudaMemcpy(g->wt.p, i_wt.data(), sizeof(uint32_t) * (size_t)m, cudaMemcpyHostToDevice));
     g->graph_bytes += sizeof(uint32_t) * (size_t)m;
   }
+  for (int64_t v = 0; v < n; ++v) g->max_degree = std::max(g->max_degree, i_rp[(size_t)v + 1] - i_rp[(size_t)v]);
   if (!identity) {
     CUDA_TRY_G(g->orig.reserve(sizeof(int32_t) * (size_t)n));
     CUDA_TRY_G(g->intl.reserve(sizeof(int32_t) * (size_t)n));
@@ -343,6 +351,7 @@ extern "C" fg_status fg_graph_create_ex(int64_t n, int64_t m, const int64_t *row
   d.S = S;
   d.nparts = g->nparts;
   d.m = (uint64_t)m;
+  d.max_deg = g->max_degree;
   d.rp = g->rp.as<uint32_t>();
   d.adj = g->adj.as<uint32_t>();
   d.wt = wt ? g->wt.as<uint32_t>() : nullptr;
@@ -417,7 +426,7 @@ fg_status ensure_engine_ws(fg_graph *g, int qtype, int64_t nb, uint64_t e_cap, b
     CUDA_TRY(ws.pend.reserve(pend_bytes));
     ws.pend_clean = false;
   }
-  CUDA_TRY(ws.qbest.reserve(4 * (size_t)nb));
+  CUDA_TRY(ws.qbest.reserve(8 * (size_t)nb));
   CUDA_TRY(ws.blocksum.reserve(8 * (size_t)blocks));
   CUDA_TRY(ws.e_key.reserve(4 * e_cap));
   CUDA_TRY(ws.e_op.reserve(8 * e_cap));
@@ -467,6 +476,8 @@ fg_status run_batch(fg_graph *g, int qtype, const int32_t *src_in, int32_t nq, u
   if (o.mode != FG_MODE_BUFFERED && o.mode != FG_MODE_PLAIN) return fail(FG_ERR_INVALID_ARG, "unknown mode");
   if (o.sched != FG_SCHED_FIFO && o.sched != FG_SCHED_PRIORITY) return fail(FG_ERR_INVALID_ARG, "unknown sched");
   if (o.query_batch < 0) return fail(FG_ERR_INVALID_ARG, "query_batch must be >= 0");
+  if (o.threads_per_vertex != 0 && o.threads_per_vertex != 1 && o.threads_per_vertex != 32)
+    return fail(FG_ERR_INVALID_ARG, "threads_per_vertex must be 0, 1 or 32");
   if (qtype == Q_PPR) o.sched = FG_SCHED_FIFO;  // PPR buffers are scheduled first-in first-out
   const uint32_t max_rounds = o.max_rounds ? o.max_rounds : 1000000u;
   const uint64_t watchdog_ns = (uint64_t)(o.watchdog_ms ? o.watchdog_ms : 30000u) * 1000000ull;
@@ -527,7 +538,7 @@ fg_status run_batch(fg_graph *g, int qtype, const int32_t *src_in, int32_t nq, u
     // the arena holds every seed operation of a launch; beyond that a round's
     // overflow spills losslessly into the pending bitmaps
     uint64_t e_cap = o.emit_capacity ? o.emit_capacity
-                                     : std::min<uint64_t>(1ull << 26, std::max<uint64_t>(1ull << 20, 16 * K));
+                                     : std::min<uint64_t>(1ull << 28, std::max<uint64_t>(1ull << 22, 64 * K));
     e_cap = std::min<uint64_t>(std::max<uint64_t>(e_cap, (uint64_t)nb), 1ull << 31);
     if (g->engine_qtype != qtype) {
       CUDA_TRY(engine_grid_size(qtype, g->S, &g->engine_blocks, &g->engine_threads, &g->engine_smem));
@@ -580,6 +591,9 @@ fg_status run_batch(fg_graph *g, int qtype, const int32_t *src_in, int32_t nq, u
       a.yield_edges = o.yield_edges;
       a.max_rounds = max_rounds;
       a.watchdog_ns = watchdog_ns;
+      // lane-per-vertex expansion only on request (measured slower than the
+      // warp-shared merge-path on the road-like grid)
+      a.lanes = (o.threads_per_vertex == 1 && g->max_degree <= 8) ? 1u : 0u;
       CUDA_TRY(launch_engine(a, g->engine_blocks, g->engine_threads, g->engine_smem, stream));
       ++launches;
       if (qtype == Q_PPR) {
@@ -723,8 +737,12 @@ extern "C" fg_status fg_sync(void *stream_v) {
     if (first == FG_OK && c.status != 0) {
       const char *names[] = {"ok", "invalid argument", "out of memory", "CUDA error", "watchdog timeout",
                              "operation buffer overflow", "distance overflow", "unsupported"};
+      const char *sites[] = {"", " (device-wide barrier wait)", " (partition staging wait)",
+                             " (visit step limit)", " (max_rounds)", " (source id out of range)",
+                             " (operation arena)", " (vertex degree out of range)"};
       const int k = c.status >= 0 && c.status <= 7 ? c.status : 3;
-      first = fail((fg_status)c.status, "device reported: %s", names[k]);
+      const unsigned si = c.site <= 7 ? c.site : 0;
+      first = fail((fg_status)c.status, "device reported: %s%s", names[k], sites[si]);
     }
     std::lock_guard<std::mutex> lp(g_pending_mu);
     g_slot_pool.push_back(p.host);

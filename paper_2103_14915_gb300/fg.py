@@ -45,7 +45,7 @@ class fg_opts(ctypes.Structure):
                 ("sched_window", ctypes.c_uint32), ("delta", ctypes.c_uint32), ("bucket", ctypes.c_uint32),
                 ("yield_edges", ctypes.c_uint64), ("max_rounds", ctypes.c_uint32),
                 ("watchdog_ms", ctypes.c_uint32), ("emit_capacity", ctypes.c_uint64),
-                ("host_io", ctypes.c_int32), ("query_batch", ctypes.c_int32)]
+                ("host_io", ctypes.c_int32), ("query_batch", ctypes.c_int32), ("threads_per_vertex", ctypes.c_int32)]
 
 
 class fg_stats_t(ctypes.Structure):

@@ -45,7 +45,7 @@ class DevGraph:
         srcs = np.ascontiguousarray(srcs, dtype=np.int32)
         s_d = torch.from_numpy(srcs).to(DEV)
         out = torch.empty((len(srcs), self.g.n), dtype=torch.int32, device=DEV)
-        o = fg.fg_default_opts(**opts)
+        o = fg.fg_default_opts(**dict(dict(watchdog_ms=10000), **opts))
         f = fg.fg_sssp_batch if kind == "sssp" else fg.fg_bfs_batch
         fg.check(f(self.h, s_d, len(srcs), out, None, o))
         st = fg.fg_sync()
@@ -57,7 +57,7 @@ class DevGraph:
         p = torch.empty((len(srcs), self.g.n), dtype=torch.float32, device=DEV)
         r = torch.empty_like(p)
         mass = torch.empty(len(srcs), dtype=torch.float64, device=DEV)
-        o = fg.fg_default_opts(**opts)
+        o = fg.fg_default_opts(**dict(dict(watchdog_ms=10000), **opts))
         fg.check(fg.fg_ppr_batch(self.h, s_d, len(srcs), alpha, eps, p, r, mass, None, o))
         st = fg.fg_sync()
         return st, p.cpu().numpy(), r.cpu().numpy(), mass.cpu().numpy()
@@ -119,6 +119,8 @@ OPTS = [
     dict(emit_capacity=1),
     dict(emit_capacity=7, yield_edges=3),
     dict(mode=fg.FG_MODE_PLAIN),
+    dict(threads_per_vertex=1),
+    dict(threads_per_vertex=1, delta=300, sched=fg.FG_SCHED_PRIORITY),
 ]
 
 
