@@ -106,6 +106,9 @@ typedef struct {
     uint64_t yields;        /* visits that left work behind (yield or budget) */
     uint64_t launches;      /* kernels launched by the batch */
     uint64_t max_round_ops; /* most operations buffered in one round */
+    uint64_t phase_ns[6];   /* device time per phase, summed over rounds, between device-wide
+                               barriers: tile init, seeding, scan A, scan B (scheduling),
+                               scatter into bins, intra-partition processing */
 } fg_stats_t;
 
 typedef struct {

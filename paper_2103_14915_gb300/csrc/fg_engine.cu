@@ -53,7 +53,11 @@ struct WarpSmem {
   uint32_t *pfx;    // [nw] exclusive popcount prefix of cur
 };
 
-__host__ __device__ inline size_t warp_smem_words(int S) { return (size_t)S + 5u * (size_t)(S / 32); }
+// Per-warp area in words, rounded up to 16 bytes so every warp's slice is
+// 16-byte aligned (the dynamic shared memory base is).
+__host__ __device__ inline size_t warp_smem_words(int S) {
+  return ((size_t)S + 5u * (size_t)(S / 32) + 3u) & ~(size_t)3u;
+}
 
 
 // ---------------------------------------------------------------------------
@@ -141,8 +145,26 @@ __device__ __forceinline__ uint32_t frontier_select(const WarpSmem &w, int nw, u
   return (uint32_t)lo * 32u + (uint32_t)bit;
 }
 
-__device__ __forceinline__ uint32_t slice_index(const DevGraph &g, uint32_t internal) {
-  return g.orig ? (uint32_t)g.orig[internal] : internal;
+// Query state is kept in partition-major (internal) vertex order, so a
+// partition's slice of one query is a contiguous run of S values.
+__device__ __forceinline__ void load_slice(uint32_t *dst, const uint32_t *src, int Sp, int lane) {
+  if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0 && (Sp & 3) == 0) {
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    for (int i = lane; i < (Sp >> 2); i += 32) d4[i] = __ldcg(s4 + i);
+  } else {
+    for (int i = lane; i < Sp; i += 32) dst[i] = __ldcg(src + i);
+  }
+}
+
+__device__ __forceinline__ void store_slice(uint32_t *dst, const uint32_t *src, int Sp, int lane) {
+  if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0 && (Sp & 3) == 0) {
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    for (int i = lane; i < (Sp >> 2); i += 32) __stcg(d4 + i, s4[i]);
+  } else {
+    for (int i = lane; i < Sp; i += 32) __stcg(dst + i, src[i]);
+  }
 }
 
 // CSR view of the resident partition. rp is indexed by the local vertex id and
@@ -214,11 +236,7 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
   }
 
   // 1. stage the query's slice of this partition (bypassing L1)
-  if (g.orig) {
-    for (int i = lane; i < Sp; i += 32) w.d[i] = __ldcg(drow + g.orig[base + i]);
-  } else {
-    for (int i = lane; i < Sp; i += 32) w.d[i] = __ldcg(drow + base + i);
-  }
+  load_slice(w.d, drow + base, Sp, lane);
   for (int i = Sp + lane; i < S; i += 32) w.d[i] = kInf;
   for (int wd = lane; wd < nw; wd += 32) {
     w.cur[wd] = 0u; w.nxt[wd] = 0u; w.far[wd] = 0u; w.carry[wd] = 0u;
@@ -362,7 +380,7 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
             if ((uint32_t)j < deg) {
               if ((u[j] >> g.slog2) == p) {
                 relax_local(w, u[j] & (uint32_t)(S - 1), nd[j], T, Ty);
-              } else if (nd[j] < a.dist[(size_t)q * (size_t)g.n + slice_index(g, u[j])]) {
+              } else if (nd[j] < a.dist[(size_t)q * (size_t)g.n + u[j]]) {
                 extm |= 1u << j;
               }
             }
@@ -416,7 +434,7 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
             if ((u >> g.slog2) == p) {
               relax_local(w, u & (uint32_t)(S - 1), nd, T, Ty);
             } else {
-              ext = nd < a.dist[(size_t)q * (size_t)g.n + slice_index(g, u)];
+              ext = nd < a.dist[(size_t)q * (size_t)g.n + u];
             }
           }
           const uint32_t pk = (u >> g.slog2) * nq + q;
@@ -460,11 +478,8 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
     ctr.yields++;
   }
   // 6. write the slice back
-  if (g.orig) {
-    for (int i = lane; i < Sp; i += 32) __stcg(drow + g.orig[base + i], w.d[i]);
-  } else {
-    for (int i = lane; i < Sp; i += 32) __stcg(drow + base + i, w.d[i]);
-  }
+  __syncwarp();
+  store_slice(drow + base, w.d, Sp, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -502,7 +517,7 @@ __device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, c
     return;
   }
 
-  for (int i = lane; i < Sp; i += 32) rs[i] = __ldcg(rrow + slice_index(g, base + i));
+  load_slice(w.d, reinterpret_cast<const uint32_t *>(rrow + base), Sp, lane);
   for (int i = Sp + lane; i < S; i += 32) rs[i] = 0.f;
   for (int wd = lane; wd < nw; wd += 32) {
     w.cur[wd] = 0u; w.nxt[wd] = 0u; w.carry[wd] = 0u;
@@ -591,7 +606,7 @@ __device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, c
       float rho = 0.f, inc_l = 0.f;
       if (valid) {
         rho = atomicExch(&rs[v], 0.f);
-        const uint32_t gi = slice_index(g, base + v);
+        const uint32_t gi = base + v;
         const float pe = __ldcg(prow + gi), ce = __ldcg(crow + gi);
         const float y = __fsub_rn(__fmul_rn(alpha, rho), ce);
         const float tsum = __fadd_rn(pe, y);
@@ -656,7 +671,8 @@ __device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, c
     a.dirty[key] = 1u;
     ctr.yields++;
   }
-  for (int i = lane; i < Sp; i += 32) __stcg(rrow + slice_index(g, base + i), rs[i]);
+  __syncwarp();
+  store_slice(reinterpret_cast<uint32_t *>(rrow + base), w.d, Sp, lane);
 }
 
 // Buffer skipped by priority scheduling this round (SSSP/BFS). No warp stages
@@ -676,7 +692,7 @@ __device__ void carry_item(const EngineArgs &a, uint4 item, uint32_t item_prio) 
   bool any = false;
   for (uint32_t j = lane; j < cnt; j += 32) {
     const uint2 o = __ldcg(a.b_op + off + j);
-    const uint32_t old = atomicMin(drow + slice_index(g, base + o.x), o.y);
+    const uint32_t old = atomicMin(drow + base + o.x, o.y);
     if (o.y < old) {
       atomicOr(pend + (o.x >> 5), 1u << (o.x & 31));
       any = true;
@@ -734,6 +750,17 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
   // every block reads the generation before its first arrival, so all agree
   unsigned gen = *reinterpret_cast<volatile unsigned *>(&c->bar_gen);
   Counters ctr;
+  // phase clock of block 0 (device time between device-wide barriers)
+  uint64_t t_prev = (blockIdx.x == 0 && threadIdx.x == 0) ? global_ns() : 0ull;
+  unsigned long long ph[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+#define FG_PHASE(k)                                             \
+  do {                                                          \
+    if (blockIdx.x == 0 && threadIdx.x == 0) {                  \
+      const uint64_t t_now = global_ns();                       \
+      ph[k] += t_now - t_prev;                                  \
+      t_prev = t_now;                                           \
+    }                                                           \
+  } while (0)
   const uint64_t K = (uint64_t)a.g.nparts * (uint64_t)a.nq;
   const uint64_t per_blk = (K + gridDim.x - 1) / gridDim.x;
   const uint64_t k0 = umin64(K, (uint64_t)blockIdx.x * per_blk);
@@ -757,6 +784,7 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
     fill_u32(a.dirty, K, 0u, tid, nthr);
   }
   if (!grid_barrier(c, gen, a.watchdog_ns)) goto done;
+  FG_PHASE(0);
 
   // ---- INIT: seed operations (InitBuffers, second half) ----
   for (uint32_t q0 = gwarp * 32u; q0 < (uint32_t)a.nq; q0 += nwarps * 32u) {
@@ -778,6 +806,7 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
     if (!ok) raise_status(c, FG_ERR_BIN_OVERFLOW, kSiteArena);
   }
   if (!grid_barrier(c, gen, a.watchdog_ns)) goto done;
+  FG_PHASE(1);
 
   for (uint32_t round = 0;; ++round) {
     // best pending value per query: written in SCAN-A, read in SCAN-B and PROCESS,
@@ -804,6 +833,7 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
       }
     }
     if (!grid_barrier(c, gen, a.watchdog_ns)) goto done;
+    FG_PHASE(2);
     // ---- SCAN-B: work items, bin offsets, buffer reset ----
     unsigned long long tot_ops, tot_items, emitted;
     {
@@ -883,6 +913,7 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
       }
     }
     if (!grid_barrier(c, gen, a.watchdog_ns)) goto done;
+    FG_PHASE(3);
     // ---- SCATTER: arena -> bins ordered by (partition, query) ----
     {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -916,6 +947,7 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
       (void)tot_ops;
     }
     if (!grid_barrier(c, gen, a.watchdog_ns)) goto done;
+    FG_PHASE(4);
     // ---- PROCESS: IntraPartProcess of every work item ----
     // Warps claim kWarpClaim consecutive items at a time (ordered by
     // partition, then query, so one warp's items share the partition's CSR in
@@ -956,8 +988,15 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
       }
     }
     if (!grid_barrier(c, gen, a.watchdog_ns)) goto done;
+    FG_PHASE(5);
   }
 done:
+#undef FG_PHASE
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const uint64_t t_now = global_ns();
+    ph[3] += t_now - t_prev;  // the final scan that found no work
+    for (int k = 0; k < 6; ++k) atomicAdd(&c->phase_ns[k], ph[k]);
+  }
   {
     const unsigned long long sp = warp_sum(ctr.spills), yl = warp_sum(ctr.yields);
     if (lane == 0) {
@@ -973,30 +1012,46 @@ done:
 // Per-query mass check (PPR): fold the Kahan compensation into the estimate
 // (p_out = p - c, FP32) and accumulate sum(p_out) + sum(r) in FP64.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) ppr_finalize_kernel(float *p, const float *cmp, const float *r, int64_t n,
+__global__ void __launch_bounds__(256) ppr_finalize_kernel(const float *p, const float *cmp, const float *r,
+                                                           float *p_out, float *r_out, const int32_t *orig, int64_t n,
                                                            int64_t chunks, double *mass) {
   __shared__ double s_red[8];
   const int64_t q = blockIdx.x / chunks, ch = blockIdx.x % chunks;
   const int64_t per = (n + chunks - 1) / chunks;
   const int64_t i0 = ch * per, i1 = i0 + per < n ? i0 + per : n;
-  float *prow = p + q * n;
+  const float *prow = p + q * n;
   const float *crow = cmp + q * n;
   const float *rrow = r + q * n;
+  float *porow = p_out + q * n;
+  float *rorow = r_out ? r_out + q * n : nullptr;
   double acc = 0.0;
   for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const float pf = __fsub_rn(prow[i], crow[i]);
-    prow[i] = pf;
-    acc += (double)pf + (double)rrow[i];
+    const float rf = rrow[i];
+    const int64_t o = orig ? (int64_t)orig[i] : i;
+    porow[o] = pf;
+    if (rorow && rorow != rrow) rorow[o] = rf;
+    acc += (double)pf + (double)rf;
   }
   if (mass) {
     acc = warp_sum(acc);
     if (lane_id() == 0) s_red[threadIdx.x >> 5] = acc;
-    block_sync();
+    __syncthreads();
     if (threadIdx.x == 0) {
       double t = 0.0;
       for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += s_red[i];
       atomicAdd(mass + q, t);
     }
+  }
+}
+
+// Query-major state in internal order -> caller's output in original order.
+__global__ void __launch_bounds__(256) permute_out_kernel(const uint32_t *state, uint32_t *out, const int32_t *orig,
+                                                          int64_t n, int64_t rows) {
+  const int64_t total = n * rows;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = t / n, i = t - q * n;
+    out[q * n + orig[i]] = state[t];
   }
 }
 
@@ -1033,12 +1088,26 @@ cudaError_t launch_engine(const EngineArgs &a, int blocks, int threads, size_t s
   return cudaLaunchCooperativeKernel(engine_fn(a.qtype), dim3(blocks), dim3(threads), args, smem, s);
 }
 
-cudaError_t launch_ppr_finalize(const EngineArgs &a, double *mass, float *, cudaStream_t s) {
+cudaError_t launch_ppr_finalize(const EngineArgs &a, double *mass, float *p_out, float *r_out, cudaStream_t s) {
   const int64_t n = a.g.n;
   const int64_t chunks = (n + 4095) / 4096;
   const int64_t grid = chunks * (int64_t)a.nq;
   if (grid <= 0) return cudaSuccess;
-  ppr_finalize_kernel<<<(unsigned)grid, 256, 0, s>>>(a.pr_p, a.pr_c, a.pr_r, n, chunks, mass);
+  ppr_finalize_kernel<<<(unsigned)grid, 256, 0, s>>>(a.pr_p, a.pr_c, a.pr_r, p_out, r_out, a.g.orig, n, chunks, mass);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute_out(const uint32_t *state, uint32_t *out, const int32_t *orig, int64_t n, int64_t rows,
+                               cudaStream_t s) {
+  const int64_t total = n * rows;
+  if (total <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int64_t want = (total + 255) / 256;
+  const unsigned grid = (unsigned)(want < (int64_t)sms * 16 ? want : (int64_t)sms * 16);
+  permute_out_kernel<<<grid, 256, 0, s>>>(state, out, orig, n, rows);
   return cudaGetLastError();
 }
 

@@ -44,6 +44,7 @@ struct Ctrl {
   unsigned int site;          // where the first status was raised (kSite*)
   unsigned long long e_cursor;  // operations reserved in the arena this round
   unsigned long long rounds, visits, edges, ops, spills, yields, max_round_ops;
+  unsigned long long phase_ns[6];  // K0, INIT, SCAN-A, SCAN-B, SCATTER, PROCESS (block 0's view)
 };
 
 struct EngineArgs {
@@ -51,7 +52,7 @@ struct EngineArgs {
   int qtype = Q_SSSP;
   int32_t nq = 0;
   const int32_t *src = nullptr;   // [nq] original ids (device)
-  // query state, query-major [nq][n], original vertex order
+  // query state, query-major [nq][n], internal (partition-major) vertex order
   uint32_t *dist = nullptr;       // SSSP / BFS
   float *pr_p = nullptr;          // PPR estimate
   float *pr_r = nullptr;          // PPR residual
@@ -103,7 +104,9 @@ struct PlainArgs {
 // kernel launchers (fg_engine.cu / fg_plain.cu); return the CUDA error of the launch
 cudaError_t engine_grid_size(int qtype, int S, int *blocks, int *threads, size_t *smem);
 cudaError_t launch_engine(const EngineArgs &a, int blocks, int threads, size_t smem, cudaStream_t s);
-cudaError_t launch_ppr_finalize(const EngineArgs &a, double *mass, float *r_out, cudaStream_t s);
+cudaError_t launch_ppr_finalize(const EngineArgs &a, double *mass, float *p_out, float *r_out, cudaStream_t s);
+cudaError_t launch_permute_out(const uint32_t *state, uint32_t *out, const int32_t *orig, int64_t n, int64_t rows,
+                               cudaStream_t s);
 cudaError_t plain_grid_size(int *blocks, int *threads);
 cudaError_t launch_plain(const PlainArgs &a, int blocks, int threads, cudaStream_t s);
 

@@ -63,12 +63,12 @@ struct DevBuf {
 
 struct Workspace {
   DevBuf cnt, prio, dirty, cur, pend, qbest, items, iprio, blocksum, e_key, e_op, b_op, ctrl;
-  DevBuf scratch_r, scratch_c, io_src, io_out, io_out2;
+  DevBuf scratch_r, scratch_c, scratch_p, state, io_src, io_out, io_out2;
   DevBuf pl_dist, pl_rr, pl_pp, pl_cc, pl_stamp, pl_f0, pl_f1, pl_sizes;
   bool pend_clean = true;
   void release_all() {
     DevBuf *all[] = {&cnt, &prio, &dirty, &cur, &pend, &qbest, &items, &iprio, &blocksum, &e_key, &e_op,
-                     &b_op, &ctrl, &scratch_r, &scratch_c, &io_src, &io_out, &io_out2, &pl_dist, &pl_rr,
+                     &b_op, &ctrl, &scratch_r, &scratch_c, &scratch_p, &state, &io_src, &io_out, &io_out2, &pl_dist, &pl_rr,
                      &pl_pp, &pl_cc, &pl_stamp, &pl_f0, &pl_f1, &pl_sizes};
     for (DevBuf *b : all) b->release();
   }
@@ -412,6 +412,7 @@ namespace {
 
 // workspace for a buffered launch of nb queries
 fg_status ensure_engine_ws(fg_graph *g, int qtype, int64_t nb, uint64_t e_cap, bool need_r, int blocks) {
+  const bool relabelled = g->dg.orig != nullptr;
   Workspace &ws = g->ws;
   const uint64_t K = (uint64_t)g->nparts * (uint64_t)nb;
   const uint64_t nw = (uint64_t)(g->S / 32);
@@ -432,9 +433,14 @@ fg_status ensure_engine_ws(fg_graph *g, int qtype, int64_t nb, uint64_t e_cap, b
   CUDA_TRY(ws.e_op.reserve(8 * e_cap));
   CUDA_TRY(ws.b_op.reserve(8 * e_cap));
   CUDA_TRY(ws.ctrl.reserve(sizeof(Ctrl)));
+  const size_t rows = (size_t)nb * (size_t)g->n;
   if (qtype == Q_PPR) {
-    CUDA_TRY(ws.scratch_c.reserve(4 * (size_t)nb * (size_t)g->n));
-    if (need_r) CUDA_TRY(ws.scratch_r.reserve(4 * (size_t)nb * (size_t)g->n));
+    // estimates, residuals (when not requested or relabelled) and Kahan terms
+    CUDA_TRY(ws.scratch_c.reserve(4 * rows));
+    if (need_r || relabelled) CUDA_TRY(ws.scratch_r.reserve(4 * rows));
+    if (relabelled) CUDA_TRY(ws.scratch_p.reserve(4 * rows));
+  } else if (relabelled) {
+    CUDA_TRY(ws.state.reserve(4 * rows));  // distances in partition-major order
   }
   return FG_OK;
 }
@@ -521,8 +527,10 @@ fg_status run_batch(fg_graph *g, int qtype, const int32_t *src_in, int32_t nq, u
   // queries per launch: bounded by the workspace (keys, pending bitmaps, PPR scratch)
   int64_t nb = o.query_batch ? o.query_batch : nq;
   {
+    const bool relabelled = g->dg.orig != nullptr;
     const double per_query = (double)g->nparts * 36.0 + (double)n / 8.0 +
-                             (qtype == Q_PPR ? (need_r ? 8.0 : 4.0) * (double)n : 0.0);
+                             (qtype == Q_PPR ? (relabelled ? 12.0 : (need_r ? 8.0 : 4.0)) * (double)n
+                                             : (relabelled ? 4.0 : 0.0) * (double)n);
     const double budget = 24e9;
     const int64_t cap_q = std::max<int64_t>(1, (int64_t)(budget / per_query));
     nb = std::min<int64_t>(nb, cap_q);
@@ -560,14 +568,15 @@ fg_status run_batch(fg_graph *g, int qtype, const int32_t *src_in, int32_t nq, u
       a.nq = (int32_t)cnt_q;
       a.src = src + q0;
       const size_t row0 = (size_t)q0 * (size_t)n, rows = (size_t)cnt_q * (size_t)n;
+      const bool relabelled = g->dg.orig != nullptr;
       if (qtype == Q_PPR) {
-        a.pr_p = pout + row0;
-        a.pr_r = rout ? rout + row0 : ws.scratch_r.as<float>();
+        a.pr_p = relabelled ? ws.scratch_p.as<float>() : pout + row0;
+        a.pr_r = (relabelled || !rout) ? ws.scratch_r.as<float>() : rout + row0;
         a.pr_c = ws.scratch_c.as<float>();
         a.alpha = alpha;
         a.eps = eps;
       } else {
-        a.dist = dist + row0;
+        a.dist = relabelled ? ws.state.as<uint32_t>() : dist + row0;
       }
       (void)rows;
       a.cnt = ws.cnt.as<uint32_t>();
@@ -597,8 +606,13 @@ fg_status run_batch(fg_graph *g, int qtype, const int32_t *src_in, int32_t nq, u
       CUDA_TRY(launch_engine(a, g->engine_blocks, g->engine_threads, g->engine_smem, stream));
       ++launches;
       if (qtype == Q_PPR) {
+        // fold the Kahan terms, mass per query, and (if relabelled) back to original order
         if (mass && q0 == 0) CUDA_TRY(cudaMemsetAsync(mass, 0, 8 * (size_t)nq, stream));
-        CUDA_TRY(launch_ppr_finalize(a, mass ? mass + q0 : nullptr, nullptr, stream));
+        CUDA_TRY(launch_ppr_finalize(a, mass ? mass + q0 : nullptr, pout + row0, rout ? rout + row0 : nullptr,
+                                     stream));
+        ++launches;
+      } else if (relabelled) {
+        CUDA_TRY(launch_permute_out(a.dist, dist + row0, g->dg.orig, n, cnt_q, stream));
         ++launches;
       }
     }
@@ -643,13 +657,15 @@ fg_status run_batch(fg_graph *g, int qtype, const int32_t *src_in, int32_t nq, u
         ++launches;
       }
       if (qtype == Q_PPR) {
+        // the plain kernel already wrote original order: fold in place
         EngineArgs f;
         f.g = g->dg;
+        f.g.orig = nullptr;
         f.nq = (int32_t)cnt_q;
         f.pr_p = pout + (size_t)q0 * (size_t)n;
         f.pr_r = rout ? rout + (size_t)q0 * (size_t)n : ws.scratch_r.as<float>();
         f.pr_c = ws.scratch_c.as<float>();
-        CUDA_TRY(launch_ppr_finalize(f, mass ? mass + q0 : nullptr, nullptr, stream));
+        CUDA_TRY(launch_ppr_finalize(f, mass ? mass + q0 : nullptr, f.pr_p, rout ? f.pr_r : nullptr, stream));
         ++launches;
       }
     }
@@ -731,6 +747,7 @@ extern "C" fg_status fg_sync(void *stream_v) {
       s.yields = c.yields;
       s.launches = p.launches;
       s.max_round_ops = c.max_round_ops;
+      for (int k = 0; k < 6; ++k) s.phase_ns[k] = c.phase_ns[k];
       p.graph->last_stats = s;
       if (c.status != 0 && c.status != FG_ERR_OVERFLOW) p.graph->ws.pend_clean = false;
     }

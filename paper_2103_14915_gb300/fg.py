@@ -50,7 +50,15 @@ class fg_opts(ctypes.Structure):
 
 class fg_stats_t(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in
-                ("rounds", "visits", "edges", "ops", "spills", "yields", "launches", "max_round_ops")]
+                ("rounds", "visits", "edges", "ops", "spills", "yields", "launches", "max_round_ops")] + [
+                   ("phase_ns", ctypes.c_uint64 * 6)]
+
+    PHASES = ("init_tiles", "seed", "scan_a", "scan_b", "scatter", "process")
+
+    def as_dict(self):
+        d = {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "phase_ns"}
+        d["phase_ms"] = {n: round(self.phase_ns[i] / 1e6, 3) for i, n in enumerate(self.PHASES)}
+        return d
 
 
 class fg_graph_info_t(ctypes.Structure):
