@@ -307,8 +307,7 @@ def main():
         "roofline": roofline,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
-        "stats": {"bfs": {k: int(getattr(sb, k)) for k, _ in sb._fields_},
-                  "sssp": {k: int(getattr(ss, k)) for k, _ in ss._fields_}},
+        "stats": {"bfs": sb.as_dict(), "sssp": ss.as_dict()},
     }
 
     if not args.no_extras:
