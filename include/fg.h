@@ -192,6 +192,42 @@ fg_status fg_stats(const fg_graph *g, fg_stats_t *out);
 fg_status fg_partition_plan(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t method,
                             int32_t partition_vertices, int32_t *perm);
 
+/*
+ * SSSP without any allocation. The paper has no counterpart: this is a
+ * service for callers that must not allocate once running (device memory
+ * fixed up front by another pool, or independent work on other streams that
+ * must not be stalled by the device-wide synchronisation of cudaFree).
+ *
+ * Computes the same exact distances as fg_sssp_batch (dist_out uint32[nq * n],
+ * original vertex order, UINT32_MAX = unreachable), one query after another
+ * with the plain per-query kernel, on scratch compiled into the library: one
+ * 16 MiB + 512 B array of device memory per device, so the graph may have at
+ * most FG_NOALLOC_MAX_VERTICES vertices; a larger graph is rejected with
+ * FG_ERR_UNSUPPORTED before anything is enqueued. src (int32[nq]) and
+ * dist_out are DEVICE pointers owned by the caller, on the graph's device,
+ * which must be the current device. The call makes no cudaMalloc, cudaFree or
+ * host allocation, takes no fg_opts, and does not update fg_stats.
+ *
+ * Set-up: the first call on each device (with that device current) looks up
+ * the scratch's device address with cudaGetSymbolAddress and sizes the
+ * cooperative grid; make that first call before any stream capture begins.
+ * Each call clears the scratch's control block (a memset on `stream`) before
+ * its first launch; nothing else needs to start at zero.
+ *
+ * The call is synchronous: it enqueues its work on `stream`, waits for the
+ * stream, and returns device-side errors (source id out of range, distance
+ * overflow, watchdog timeout) as its result. Host-detected errors (NULL or
+ * misaligned pointers, nq <= 0, wrong current device, too many vertices) are
+ * returned before anything is enqueued.
+ *
+ * All calls on one device share the one scratch array: two calls that
+ * overlap in time on the same device (from two host threads) race, and their
+ * results are undefined. The caller serialises them.
+ */
+#define FG_NOALLOC_MAX_VERTICES (1 << 20)
+fg_status fg_sssp_batch_noalloc(const fg_graph *g, const int32_t *src, int32_t nq, uint32_t *dist_out,
+                                void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -110,4 +110,8 @@ cudaError_t launch_permute_out(const uint32_t *state, uint32_t *out, const int32
 cudaError_t plain_grid_size(int *blocks, int *threads);
 cudaError_t launch_plain(const PlainArgs &a, int blocks, int threads, cudaStream_t s);
 
+// runtime services for entry points outside fg_runtime.cpp
+fg_status report_error(fg_status s, const char *msg);  // sets fg_last_error(), returns s
+void graph_device_view(const fg_graph *g, DevGraph *dg, int *device);
+
 }  // namespace fg

@@ -766,3 +766,17 @@ extern "C" fg_status fg_sync(void *stream_v) {
   }
   return first;
 }
+
+namespace fg {
+
+fg_status report_error(fg_status s, const char *msg) {
+  t_err = msg ? msg : "";
+  return s;
+}
+
+void graph_device_view(const fg_graph *g, DevGraph *dg, int *device) {
+  *dg = g->dg;
+  *device = g->device;
+}
+
+}  // namespace fg

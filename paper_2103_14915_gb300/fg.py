@@ -69,7 +69,9 @@ class fg_graph_info_t(ctypes.Structure):
 
 EXPORTS = ("fg_default_opts", "fg_default_graph_opts", "fg_graph_create", "fg_graph_create_ex",
            "fg_graph_destroy", "fg_graph_info", "fg_sssp_batch", "fg_bfs_batch", "fg_ppr_batch", "fg_sync",
-           "fg_last_error", "fg_stats", "fg_partition_plan")
+           "fg_last_error", "fg_stats", "fg_partition_plan", "fg_sssp_batch_noalloc")
+
+FG_NOALLOC_MAX_VERTICES = 1 << 20
 
 
 def lib_path() -> Path:
@@ -101,8 +103,10 @@ def load():
     lib.fg_last_error.restype = ctypes.c_char_p
     lib.fg_stats.argtypes = [vp, ctypes.POINTER(fg_stats_t)]
     lib.fg_partition_plan.argtypes = [i64, vp, vp, i32, i32, vp]
+    lib.fg_sssp_batch_noalloc.argtypes = [vp, vp, i32, vp, vp]
     for name in ("fg_graph_create", "fg_graph_create_ex", "fg_graph_destroy", "fg_graph_info", "fg_sssp_batch",
-                 "fg_bfs_batch", "fg_ppr_batch", "fg_sync", "fg_stats", "fg_partition_plan"):
+                 "fg_bfs_batch", "fg_ppr_batch", "fg_sync", "fg_stats", "fg_partition_plan",
+                 "fg_sssp_batch_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -216,3 +220,8 @@ def fg_stats(g):
 
 def fg_partition_plan(n, row_ptr, col, method, partition_vertices, perm_out) -> int:
     return load().fg_partition_plan(n, _ptr(row_ptr), _ptr(col), method, partition_vertices, _ptr(perm_out))
+
+
+def fg_sssp_batch_noalloc(g, src, nq, dist_out, stream=None) -> int:
+    """Synchronous; device pointers only; graph of at most FG_NOALLOC_MAX_VERTICES vertices."""
+    return load().fg_sssp_batch_noalloc(g, _ptr(src), nq, _ptr(dist_out), _stream(stream))

@@ -86,6 +86,7 @@ def test_batch_rejects_null_graph(lib):
     assert fg.fg_sssp_batch(None, src, 4, out) == fg.FG_ERR_INVALID_ARG
     assert fg.fg_bfs_batch(None, src, 4, out) == fg.FG_ERR_INVALID_ARG
     assert fg.fg_ppr_batch(None, src, 4, 0.15, 1e-4, out) == fg.FG_ERR_INVALID_ARG
+    assert fg.fg_sssp_batch_noalloc(None, src, 4, out) == fg.FG_ERR_INVALID_ARG
     st, _ = fg.fg_graph_info(None)
     assert st == fg.FG_ERR_INVALID_ARG
     assert fg.fg_graph_destroy(None) == fg.FG_OK
