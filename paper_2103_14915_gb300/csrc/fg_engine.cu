@@ -33,9 +33,10 @@ namespace fg {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr uint32_t kMaxVisitSteps = 1u << 22;
-constexpr uint32_t kWarpClaim = 2;              // work items a warp claims at once
-constexpr int kLaneMaxDeg = 8;                   // lane-per-vertex expansion for max out-degree <= 8  // relax/push steps of one visit before the watchdog fires
+constexpr uint32_t kMaxVisitSteps = 1u << 22;  // relax/push steps of one visit before the watchdog fires
+constexpr uint32_t kBlockChunk = 16;            // work items a block claims at once
+constexpr uint32_t kArenaChunk = 64;            // arena slots a warp reserves at once (>= 32)
+constexpr int kLaneMaxDeg = 8;                  // lane-per-vertex expansion for max out-degree <= 8
 
 // Per-warp counters. visits and edges are lane-uniform; spills and yields are
 // summed over the lanes when flushed.
@@ -62,20 +63,51 @@ __host__ __device__ inline size_t warp_smem_words(int S) {
 
 // ---------------------------------------------------------------------------
 // Warp-collective append of at most one operation per lane to the arena.
-// Reserves with one atomicAdd per warp; per-buffer counts (and best value for
-// priority scheduling) are aggregated across lanes that target the same
-// buffer (__match_any_sync). Returns false for lanes whose operation did not
-// fit (the caller spills it); lanes without an operation return true.
+// Per-buffer counts (and best value for priority scheduling) are aggregated
+// across lanes that target the same buffer (__match_any_sync). Returns false
+// for lanes whose operation did not fit (the caller spills it); lanes without
+// an operation return true.
+//
+// Slots come from the warp's ArenaSlots: the warp reserves kArenaChunk slots
+// of the arena at a time, so the device-wide cursor is touched once per chunk
+// rather than once per append (a returning atomic on one address that every
+// warp of the grid shares). Reserved slots a warp does not fill become holes
+// (kInvalidKey) that SCATTER skips. Without ArenaSlots (seeding), each call
+// reserves exactly what it appends.
 // ---------------------------------------------------------------------------
+struct ArenaSlots {
+  unsigned long long pos = 0, end = 0;  // lane-uniform: [pos, end) reserved, not yet written
+};
+
+__device__ __forceinline__ void release_slots(const EngineArgs &a, ArenaSlots &sl) {
+  const int lane = lane_id();
+  const unsigned long long lim = sl.end < a.e_cap ? sl.end : a.e_cap;
+  for (unsigned long long s = sl.pos + (unsigned long long)lane; s < lim; s += 32ull) a.e_key[s] = kInvalidKey;
+  sl.pos = sl.end;
+}
+
 __device__ __forceinline__ bool emit_ops(const EngineArgs &a, bool has, uint32_t key, uint32_t lv,
-                                         uint32_t val, bool track_prio) {
+                                         uint32_t val, bool track_prio, ArenaSlots *sl = nullptr) {
   const unsigned m = __ballot_sync(kFull, has);
   if (m == 0) return true;
   const int lane = lane_id();
-  const int leader = __ffs(m) - 1;
+  const unsigned n = (unsigned)__popc(m);
   unsigned long long base = 0;
-  if (lane == leader) base = atomicAdd(&a.ctrl->e_cursor, (unsigned long long)__popc(m));
-  base = __shfl_sync(kFull, base, leader);
+  if (sl != nullptr) {
+    if (sl->pos + n > sl->end) {
+      release_slots(a, *sl);
+      if (lane == 0) base = atomicAdd(&a.ctrl->e_cursor, (unsigned long long)kArenaChunk);
+      base = __shfl_sync(kFull, base, 0);
+      sl->pos = base;
+      sl->end = base + kArenaChunk;
+    }
+    base = sl->pos;
+    sl->pos += n;
+  } else {
+    const int leader = __ffs(m) - 1;
+    if (lane == leader) base = atomicAdd(&a.ctrl->e_cursor, (unsigned long long)n);
+    base = __shfl_sync(kFull, base, leader);
+  }
   const unsigned long long slot = base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
   const bool fits = has && slot < a.e_cap;
   if (fits) {
@@ -218,7 +250,7 @@ __device__ __forceinline__ void relax_local(const WarpSmem &w, uint32_t lu, uint
 // ---------------------------------------------------------------------------
 template <int QT, bool LANES>
 __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, uint32_t qbound, const PartView &pv,
-                           Counters &ctr) {
+                           Counters &ctr, ArenaSlots &sl) {
   const DevGraph &g = a.g;
   const int lane = lane_id();
   const uint32_t key = item.x, off = item.y, cnt = item.z, flags = item.w;
@@ -390,7 +422,7 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
             for (int j = 0; j < kLaneMaxDeg; ++j) {
               const bool e = (extm >> j) & 1u;
               const uint32_t pk = (u[j] >> g.slog2) * nq + q;
-              if (!emit_ops(a, e, pk, u[j] & (uint32_t)(S - 1), nd[j], true)) {
+              if (!emit_ops(a, e, pk, u[j] & (uint32_t)(S - 1), nd[j], true, &sl)) {
                 atomicOr(&w.carry[v >> 5], 1u << (v & 31));
                 ctr.spills++;
               }
@@ -438,7 +470,7 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
             }
           }
           const uint32_t pk = (u >> g.slog2) * nq + q;
-          if (!emit_ops(a, ext, pk, u & (uint32_t)(S - 1), nd, true)) {
+          if (!emit_ops(a, ext, pk, u & (uint32_t)(S - 1), nd, true, &sl)) {
             atomicOr(&w.carry[vL >> 5], 1u << (vL & 31));
             ctr.spills++;
           }
@@ -727,11 +759,56 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
   return ex;
 }
 
+// Block-level work claiming. *claim packs (end << 32 | next) for the block's
+// current chunk of item indices; the one warp that draws next == end refills
+// the chunk from the device-wide counter, warps that draw past the end wait
+// for the refill. Chunks are consecutive items (ordered by partition, then
+// query), so the warps of one block mostly visit the same partition and read
+// its CSR through the SM's L1. Called by one lane; returns an index >= tot
+// when the round has no work left for this block.
+__device__ uint32_t claim_item(Ctrl *c, unsigned long long *claim, volatile int *done, uint32_t tot,
+                               uint64_t watchdog_ns) {
+  uint64_t t0 = 0;
+  unsigned spins = 0;
+  for (;;) {
+    if (*done) return kInvalidKey;
+    const unsigned long long old = atomicAdd(claim, 1ull);
+    const uint32_t pos = (uint32_t)old, end = (uint32_t)(old >> 32);
+    if (pos < end) return pos;
+    if (pos == end) {
+      uint32_t b = atomicAdd(&c->item_next, kBlockChunk);
+      if (ld_volatile_i32(&c->abort)) b = tot;
+      if (b >= tot) {
+        *done = 1;
+        return kInvalidKey;
+      }
+      const uint32_t e = min(tot, b + kBlockChunk);
+      atomicExch(claim, ((unsigned long long)e << 32) | (unsigned long long)(b + 1u));
+      return b;
+    }
+    // another warp is refilling: wait until the chunk end moves (bounded)
+    while ((uint32_t)(*reinterpret_cast<volatile unsigned long long *>(claim) >> 32) == end && !*done) {
+      if ((++spins & 63u) == 0) {
+        const uint64_t t = global_ns();
+        if (t0 == 0) t0 = t;
+        else if (t - t0 > watchdog_ns) {
+          raise_status(c, FG_ERR_TIMEOUT, kSiteClaim);
+          *done = 1;
+          return kInvalidKey;
+        }
+      }
+      __nanosleep(32);
+    }
+  }
+}
+
 template <int QT>
 __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
   extern __shared__ __align__(16) uint32_t smem_dyn[];
   __shared__ unsigned long long s_scan[kWarps + 1];
   __shared__ unsigned long long s_pre[2];
+  __shared__ unsigned long long s_claim;  // block's chunk of work items (claim_item)
+  __shared__ int s_claim_done;
   constexpr bool kPPR = (QT == Q_PPR);
 
   const int lane = lane_id(), wid = threadIdx.x >> 5;
@@ -920,6 +997,10 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
         c->e_cursor = 0ull;
         c->item_next = 0u;
       }
+      if (threadIdx.x == 0) {  // visible to the block after the barrier below
+        s_claim = 0ull;
+        s_claim_done = 0;
+      }
       if (!kPPR && a.sched == FG_SCHED_PRIORITY)
         for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < (uint32_t)a.nq; i += gridDim.x * kThreads)
           qb_nxt[i] = kInf;
@@ -949,43 +1030,38 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
     if (!grid_barrier(c, gen, a.watchdog_ns)) goto done;
     FG_PHASE(4);
     // ---- PROCESS: IntraPartProcess of every work item ----
-    // Warps claim kWarpClaim consecutive items at a time (ordered by
-    // partition, then query, so one warp's items share the partition's CSR in
-    // L1). The resident partition lives in L2: the graph and the round's
-    // active state slices fit in it. No block-level synchronisation here.
+    // Items are handed out by claim_item (block-level chunks). The resident
+    // partition lives in L1/L2: the graph and the round's active state slices
+    // fit in L2. No block-level synchronisation here.
     {
+      ArenaSlots sl;
       for (;;) {
-        uint32_t i0 = 0;
-        if (lane == 0) {
-          i0 = atomicAdd(&c->item_next, kWarpClaim);
-          if (ld_volatile_i32(&c->abort)) i0 = 0xFFFFFFFFu;
-        }
-        i0 = __shfl_sync(kFull, i0, 0);
-        if (i0 >= (uint32_t)tot_items) break;
-        const uint32_t i1 = (uint32_t)umin64(tot_items, (uint64_t)i0 + kWarpClaim);
-        for (uint32_t idx = i0; idx < i1; ++idx) {
-          const uint4 it = __ldcg(a.items + idx);
-          const uint32_t p = it.x / (uint32_t)a.nq;
-          PartView pv;
-          pv.rp = a.g.rp + ((size_t)p << a.g.slog2);
-          pv.adj = a.g.adj;
-          pv.wt = a.g.wt;
-          pv.off = 0u;
-          pv.narc = (uint32_t)a.g.m;
-          pv.part = p;
-          if (!kPPR && (it.w & 2u)) {
-            carry_item(a, it, __ldcg(a.iprio + idx));
-          } else if (kPPR) {
-            visit_ppr(a, w, it, pv, ctr);
-          } else {
-            const uint32_t q = it.x - p * (uint32_t)a.nq;
-            const uint32_t qbound =
-                a.sched == FG_SCHED_PRIORITY ? sat_add_u32(__ldcg(qb_cur + q), a.sched_window) : kInf;
-            if (a.lanes) visit_dist<QT, true>(a, w, it, qbound, pv, ctr);
-            else visit_dist<QT, false>(a, w, it, qbound, pv, ctr);
-          }
+        uint32_t idx = 0;
+        if (lane == 0) idx = claim_item(c, &s_claim, &s_claim_done, (uint32_t)tot_items, a.watchdog_ns);
+        idx = __shfl_sync(kFull, idx, 0);
+        if (idx >= (uint32_t)tot_items) break;
+        const uint4 it = __ldcg(a.items + idx);
+        const uint32_t p = it.x / (uint32_t)a.nq;
+        PartView pv;
+        pv.rp = a.g.rp + ((size_t)p << a.g.slog2);
+        pv.adj = a.g.adj;
+        pv.wt = a.g.wt;
+        pv.off = 0u;
+        pv.narc = (uint32_t)a.g.m;
+        pv.part = p;
+        if (!kPPR && (it.w & 2u)) {
+          carry_item(a, it, __ldcg(a.iprio + idx));
+        } else if (kPPR) {
+          visit_ppr(a, w, it, pv, ctr);
+        } else {
+          const uint32_t q = it.x - p * (uint32_t)a.nq;
+          const uint32_t qbound =
+              a.sched == FG_SCHED_PRIORITY ? sat_add_u32(__ldcg(qb_cur + q), a.sched_window) : kInf;
+          if (a.lanes) visit_dist<QT, true>(a, w, it, qbound, pv, ctr, sl);
+          else visit_dist<QT, false>(a, w, it, qbound, pv, ctr, sl);
         }
       }
+      release_slots(a, sl);  // before the barrier: SCATTER reads every reserved slot
     }
     if (!grid_barrier(c, gen, a.watchdog_ns)) goto done;
     FG_PHASE(5);

@@ -16,7 +16,7 @@ constexpr uint32_t kInvalidKey = 0xFFFFFFFFu;
 
 // where a device status was raised (reported by fg_sync)
 enum : unsigned { kSiteNone = 0, kSiteBarrier = 1, kSiteStage = 2, kSiteVisit = 3, kSiteRounds = 4,
-                  kSiteSource = 5, kSiteArena = 6, kSiteDegree = 7 };
+                  kSiteSource = 5, kSiteArena = 6, kSiteDegree = 7, kSiteClaim = 8 };
 
 // Graph in partition-major ("internal") vertex order. Partition j holds the
 // internal ids [j*S, (j+1)*S); S = 1 << slog2.

@@ -756,9 +756,9 @@ extern "C" fg_status fg_sync(void *stream_v) {
                              "operation buffer overflow", "distance overflow", "unsupported"};
       const char *sites[] = {"", " (device-wide barrier wait)", " (partition staging wait)",
                              " (visit step limit)", " (max_rounds)", " (source id out of range)",
-                             " (operation arena)", " (vertex degree out of range)"};
+                             " (operation arena)", " (vertex degree out of range)", " (work-item claim wait)"};
       const int k = c.status >= 0 && c.status <= 7 ? c.status : 3;
-      const unsigned si = c.site <= 7 ? c.site : 0;
+      const unsigned si = c.site <= 8 ? c.site : 0;
       first = fail((fg_status)c.status, "device reported: %s%s", names[k], sites[si]);
     }
     std::lock_guard<std::mutex> lp(g_pending_mu);
