@@ -165,6 +165,49 @@ __device__ __forceinline__ uint32_t frontier_prefix(const WarpSmem &w, const Wor
 }
 
 // idx-th set bit of cur (0-based), using the prefix array.
+// Register form of the step's frontier, for partitions of at most 1024
+// vertices (at most one bitmap word per lane): lane l holds word l of cur,
+// the popcount prefix of the words before it, and the total. Selection then
+// needs shuffles only (no prefix words in shared memory, no warp sync).
+struct RegFrontier {
+  uint32_t word, ex, tot;
+};
+
+__device__ __forceinline__ RegFrontier reg_frontier(const WarpSmem &w, int nw, int lane) {
+  RegFrontier f;
+  f.word = lane < nw ? w.cur[lane] : 0u;
+  const uint32_t c = (uint32_t)__popc(f.word);
+  const uint32_t incl = warp_incl_scan(c);
+  f.ex = incl - c;
+  f.tot = __shfl_sync(kFull, incl, 31);
+  return f;
+}
+
+// Position of the r-th set bit (r counted from 0, r < popcount(x)), found by
+// halving: compare r with the popcount of the lower half at each width.
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t x, uint32_t r) {
+  uint32_t pos = 0;
+#pragma unroll
+  for (int wd = 16; wd; wd >>= 1) {
+    const uint32_t lo = (uint32_t)__popc(x & ((1u << wd) - 1u));
+    if (r >= lo) {
+      r -= lo;
+      x >>= wd;
+      pos += (uint32_t)wd;
+    }
+  }
+  return pos;
+}
+
+// Vertex (slice index) of frontier position idx < f.tot. Warp-collective:
+// every lane calls it (inactive lanes with idx = 0).
+__device__ __forceinline__ uint32_t reg_select(const RegFrontier &f, uint32_t idx) {
+  const int L = owner_lane(f.ex, idx);  // the lane whose word holds position idx
+  const uint32_t wL = __shfl_sync(kFull, f.word, L);
+  const uint32_t exL = __shfl_sync(kFull, f.ex, L);
+  return (uint32_t)L * 32u + nth_set_bit(wL, idx - exL);
+}
+
 __device__ __forceinline__ uint32_t frontier_select(const WarpSmem &w, int nw, uint32_t idx) {
   int lo = 0, hi = nw - 1;
   while (lo < hi) {
@@ -335,10 +378,15 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
       break;
     }
     uint32_t F;
+    RegFrontier rf;
+    const bool reg_front = nw <= 32;
     if (LANES) {
       uint32_t cntl = 0;
       for (int wd = wr.w0; wd < wr.w1; ++wd) cntl += __popc(w.cur[wd]);
       F = __reduce_add_sync(kFull, cntl);
+    } else if (reg_front) {
+      rf = reg_frontier(w, nw, lane);
+      F = rf.tot;
     } else {
       F = frontier_prefix(w, wr);
     }
@@ -436,8 +484,9 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
       for (uint32_t b0 = 0; b0 < F; b0 += 32) {
         const uint32_t idx = b0 + (uint32_t)lane;
         uint32_t v = 0, dv = 0, a0 = 0, deg = 0;
+        if (reg_front) v = reg_select(rf, idx < F ? idx : 0u);
         if (idx < F) {
-          v = frontier_select(w, nw, idx);
+          if (!reg_front) v = frontier_select(w, nw, idx);
           dv = w.d[v];
           a0 = pv.rp[v];
           deg = pv.rp[v + 1] - a0;
