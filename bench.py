@@ -151,6 +151,69 @@ def engine_traffic():
         return None
 
 
+def serve_stream(fg, h, g, lam, n_req, seed, lanes, max_batch, kinds=(0, 1, 2), alpha=0.15, eps=1e-6,
+                 opts=None):
+    """Poisson stream of single-source requests through the serving loop (fg_server_*).
+
+    Request i arrives at a seeded exponential-gap time, with a kind drawn
+    uniformly from `kinds` and a seeded-uniform source. The host loop submits
+    requests as their arrival time passes, polls, and releases completed ones.
+    Latency = completion seen by fg_server_poll - scheduled arrival (host
+    monotonic clock, the server's steady clock).
+    """
+    from paper_2103_14915_gb300 import inputs
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / lam, n_req)
+    arrive = np.cumsum(gaps)
+    kind = rng.choice(np.asarray(kinds, dtype=np.int32), n_req)
+    pool = inputs.sources_uniform(g, min(n_req, 65536), seed + 1)
+    src = pool[rng.integers(0, len(pool), n_req)]
+    so = fg.fg_default_server_opts(lanes=lanes, max_batch=max_batch, alpha=alpha, eps=eps)
+    for k, o in (opts or {}).items():
+        for key, v in o.items():
+            setattr(so.opts[k], key, v)
+    st, srv = fg.fg_server_create(h, so)
+    fg.check(st)
+    arr_ns = {}
+    lat = {0: [], 1: [], 2: []}
+    batch = []
+    i = done = 0
+    t0 = time.monotonic_ns()
+    first_ok = True
+    try:
+        while done < n_req:
+            now = (time.monotonic_ns() - t0) / 1e9
+            while i < n_req and arrive[i] <= now:
+                st, rid = fg.fg_server_submit(srv, int(kind[i]), int(src[i]))
+                fg.check(st)
+                arr_ns[rid] = t0 + int(arrive[i] * 1e9)
+                i += 1
+            st, ids = fg.fg_server_poll(srv, 4096)
+            if st != fg.FG_OK:
+                first_ok = False
+            for rid in ids:
+                st, info = fg.fg_server_info(srv, rid)
+                fg.check(st)
+                if info.status != fg.FG_OK:
+                    first_ok = False
+                lat[info.kind].append((info.done_ns - arr_ns.pop(rid)) / 1e6)
+                batch.append(info.batch_size)
+                fg.check(fg.fg_server_release(srv, rid))
+                done += 1
+            if not ids and i < n_req:
+                time.sleep(max(0.0, min(2e-4, arrive[i] - (time.monotonic_ns() - t0) / 1e9)))
+        t_end = time.monotonic_ns()
+    finally:
+        fg.fg_server_destroy(srv)
+    allv = np.concatenate([np.asarray(v) for v in lat.values() if v])
+    names = {0: "sssp", 1: "bfs", 2: "ppr"}
+    return {"lambda_qps": lam, "requests": n_req, "ok": first_ok,
+            "throughput_qps": n_req / ((t_end - t0) / 1e9 - 0.0),
+            "p50_ms": float(np.percentile(allv, 50)), "p99_ms": float(np.percentile(allv, 99)),
+            "per_kind_p99_ms": {names[k]: float(np.percentile(v, 99)) for k, v in lat.items() if v},
+            "mean_batch": float(np.mean(batch)), "lanes": lanes, "max_batch": max_batch}
+
+
 def run_reference(args):
     """The oracle (CPU, OpenMP over queries) on a bounded sample of the same workload."""
     ws, rank, _ = dist_env()

@@ -193,6 +193,66 @@ fg_status fg_partition_plan(int64_t n, const int64_t *row_ptr, const int32_t *co
                             int32_t partition_vertices, int32_t *perm);
 
 /*
+ * Serving loop (continuous batching). Requests -- one SSSP, BFS or PPR query
+ * from one source -- are submitted one at a time; fg_server_poll launches
+ * the waiting requests of one kind as a batch on every free lane and reports
+ * requests whose batch has completed. Each lane has its own stream, engine
+ * workspace and output rows, and by default launches on 1/lanes of the GPU's
+ * resident grid, so batches of different kinds and ages run on the device at
+ * once. A lane is free again when every request of its batch has been
+ * released. The server's device memory is fixed at creation: lanes *
+ * max_batch output rows plus each lane's engine workspace, with max_batch
+ * lowered if needed so that a full batch of every lane fits hbm_budget
+ * (admission by HBM budget). Results are bit-identical to fg_sssp_batch /
+ * fg_bfs_batch for the same source; PPR results meet the same bound as
+ * fg_ppr_batch. The graph must outlive the server. Calls on one server are
+ * serialised by the server's lock; fg_server_submit may be called from any
+ * thread.
+ */
+typedef struct fg_server fg_server;
+
+enum { FG_QUERY_SSSP = 0, FG_QUERY_BFS = 1, FG_QUERY_PPR = 2 };
+
+typedef struct {
+    uint32_t struct_size;   /* sizeof(fg_server_opts) */
+    int32_t lanes;          /* batches in flight at once, 1..64 (default 4) */
+    int32_t max_batch;      /* requests per batch (default 256; lowered to fit hbm_budget) */
+    int32_t full_grid;      /* 1: every batch launches on the whole resident grid; 0 (default): 1/lanes of it */
+    float alpha, eps;       /* PPR parameters of every PPR request (default 0.15, 1e-6) */
+    int64_t hbm_budget;     /* device bytes for all lanes' batches; 0 (default) = 60% of free memory */
+    fg_opts opts[3];        /* engine options per kind (SSSP, BFS, PPR); struct_size 0 = defaults */
+} fg_server_opts;
+
+typedef struct {
+    int32_t kind;           /* FG_QUERY_* */
+    int32_t source;         /* original vertex id */
+    int32_t status;         /* -1 while pending or running, else the fg_status of its batch */
+    int32_t batch_size;     /* requests in its batch */
+    int64_t submit_ns, launch_ns, done_ns;  /* host steady clock; done = completion seen by fg_server_poll */
+    const void *result;     /* DEVICE row, original order: uint32[n] (SSSP/BFS, UINT32_MAX = unreachable)
+                               or float[n] PPR estimates; valid from completion until release */
+    const float *residual;  /* DEVICE float[n] PPR residuals, else NULL */
+    double mass;            /* PPR: sum(p) + sum(r) in FP64; else 0 */
+} fg_request_info;
+
+void fg_default_server_opts(fg_server_opts *o);
+fg_status fg_server_create(fg_graph *g, const fg_server_opts *o, fg_server **out);
+/* Waits for the lanes' work in flight, then frees everything (outstanding results become invalid). */
+fg_status fg_server_destroy(fg_server *s);
+/* Queues one request; *id identifies it until fg_server_release. Bad kind or source: FG_ERR_INVALID_ARG. */
+fg_status fg_server_submit(fg_server *s, int32_t kind, int32_t source, uint64_t *id);
+/*
+ * Non-blocking progress step: collects completed batches, launches waiting
+ * requests on free lanes, and writes up to cap completed request ids to done
+ * (*n_done of them; the rest are reported by later polls). Returns the first
+ * error of a batch seen in this call (its requests carry it in status).
+ */
+fg_status fg_server_poll(fg_server *s, uint64_t *done, int32_t cap, int32_t *n_done);
+fg_status fg_server_info(fg_server *s, uint64_t id, fg_request_info *info);
+/* Frees a completed request's result row; its lane is reused once its whole batch is released. */
+fg_status fg_server_release(fg_server *s, uint64_t id);
+
+/*
  * SSSP without any allocation. The paper has no counterpart: this is a
  * service for callers that must not allocate once running (device memory
  * fixed up front by another pool, or independent work on other streams that

@@ -77,7 +77,17 @@ __host__ __device__ inline size_t warp_smem_words(int S) {
 // ---------------------------------------------------------------------------
 struct ArenaSlots {
   unsigned long long pos = 0, end = 0;  // lane-uniform: [pos, end) reserved, not yet written
+  unsigned long long seen = 0;          // device-wide cursor as of the last reservation
 };
+
+// Arena pressure: once a quarter of the arena is left, visits stop at their
+// next step and unvisited items are carried to the next round, so a round's
+// appends stay within the arena instead of spilling. (A spilled relaxation
+// re-marks its source vertex, and re-expanding a vertex of high degree round
+// after round multiplies the work.)
+__device__ __forceinline__ bool arena_pressed(const EngineArgs &a, unsigned long long cursor) {
+  return cursor >= a.e_cap - (a.e_cap >> 2);
+}
 
 __device__ __forceinline__ void release_slots(const EngineArgs &a, ArenaSlots &sl) {
   const int lane = lane_id();
@@ -100,6 +110,7 @@ __device__ __forceinline__ bool emit_ops(const EngineArgs &a, bool has, uint32_t
       base = __shfl_sync(kFull, base, 0);
       sl->pos = base;
       sl->end = base + kArenaChunk;
+      sl->seen = sl->end;
     }
     base = sl->pos;
     sl->pos += n;
@@ -418,6 +429,10 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
       continue;
     }
     if (a.yield_edges && vis_edges >= a.yield_edges) {  // yield heuristic 1
+      stopped = true;
+      break;
+    }
+    if (arena_pressed(a, sl.seen)) {  // leave the rest of the visit to the next round
       stopped = true;
       break;
     }
@@ -1098,7 +1113,14 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
         pv.off = 0u;
         pv.narc = (uint32_t)a.g.m;
         pv.part = p;
-        if (!kPPR && (it.w & 2u)) {
+        bool defer = !kPPR && (it.w & 2u);
+        if (!kPPR && !defer) {
+          unsigned long long cursor = 0;
+          if (lane == 0) cursor = *reinterpret_cast<volatile unsigned long long *>(&c->e_cursor);
+          cursor = __shfl_sync(kFull, cursor, 0);
+          defer = arena_pressed(a, cursor > sl.seen ? cursor : sl.seen);
+        }
+        if (defer) {
           carry_item(a, it, __ldcg(a.iprio + idx));
         } else if (kPPR) {
           visit_ppr(a, w, it, pv, ctr);

@@ -1,0 +1,90 @@
+// Host-side structures shared by the runtime (fg_runtime.cpp) and the
+// serving loop (fg_server.cpp): device buffers, per-batch workspace, the
+// graph handle and the batch launcher.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+
+#include "fg_internal.h"
+
+namespace fg {
+
+// Sets the calling thread's fg_last_error() message (printf format) and returns s.
+fg_status fail(fg_status s, const char *fmt, ...);
+
+#define CUDA_TRY(expr)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(e_ == cudaErrorMemoryAllocation ? FG_ERR_OOM : FG_ERR_CUDA, "%s: %s (%s:%d)", \
+                  #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                       \
+  } while (0)
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  cudaError_t reserve(size_t b) {
+    if (b <= bytes && p) return cudaSuccess;
+    release();
+    cudaError_t e = cudaMalloc(&p, b ? b : 16);
+    if (e == cudaSuccess) bytes = b;
+    else p = nullptr;
+    return e;
+  }
+  template <typename T>
+  T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+struct Workspace {
+  DevBuf cnt, prio, dirty, cur, pend, qbest, items, iprio, blocksum, e_key, e_op, b_op, ctrl;
+  DevBuf scratch_r, scratch_c, scratch_p, state, io_src, io_out, io_out2;
+  DevBuf pl_dist, pl_rr, pl_pp, pl_cc, pl_stamp, pl_f0, pl_f1, pl_sizes;
+  bool pend_clean = true;
+  void release_all() {
+    DevBuf *all[] = {&cnt, &prio, &dirty, &cur, &pend, &qbest, &items, &iprio, &blocksum, &e_key, &e_op,
+                     &b_op, &ctrl, &scratch_r, &scratch_c, &scratch_p, &state, &io_src, &io_out, &io_out2, &pl_dist, &pl_rr,
+                     &pl_pp, &pl_cc, &pl_stamp, &pl_f0, &pl_f1, &pl_sizes};
+    for (DevBuf *b : all) b->release();
+  }
+};
+
+}  // namespace fg
+
+// Graph handle of the C ABI: the partitioned graph on the device, its own
+// batch workspace, and the cached launch shapes.
+struct fg_graph {
+  fg::DevGraph dg;
+  int64_t n = 0, m = 0;
+  int method = FG_PART_RANGE, S = 0, slog2 = 0, nparts = 0;
+  int64_t cut = 0;
+  bool weighted = false;
+  int device = 0;
+  fg::DevBuf rp, adj, wt, orig, intl;
+  size_t graph_bytes = 0;
+  std::mutex mu;                   // guards ws, last_done and the cached launch shapes
+  cudaEvent_t last_done = nullptr;
+  bool has_last = false;
+  fg::Workspace ws;
+  fg_stats_t last_stats{};
+  int engine_blocks = 0, engine_threads = 0;
+  size_t engine_smem = 0;
+  int engine_qtype = -1;
+  uint32_t max_degree = 0;
+  int plain_blocks = 0, plain_threads = 0;
+};
+
+namespace fg {
+
+// One batch of nq queries on workspace ws (see fg_runtime.cpp).
+fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div, int qtype, const int32_t *src_in,
+                       int32_t nq, uint32_t *dist_in, float alpha, float eps, float *p_in, float *r_in,
+                       double *mass_in, void *stream_v, const fg_opts *opts_in);
+
+}  // namespace fg

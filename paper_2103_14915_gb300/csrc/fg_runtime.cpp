@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "fg_internal.h"
+#include "fg_host.h"
 
 namespace fg {
 bool partition_plan_impl(int64_t n, const int64_t *row_ptr, const int32_t *col, int method, int S, int32_t *perm);
@@ -20,9 +20,10 @@ int64_t cut_arcs_impl(int64_t n, const int64_t *row_ptr, const int32_t *col, con
 using namespace fg;
 
 namespace {
-
 thread_local std::string t_err;
+}  // namespace
 
+namespace fg {
 fg_status fail(fg_status s, const char *fmt, ...) {
   char buf[512];
   va_list ap;
@@ -32,53 +33,16 @@ fg_status fail(fg_status s, const char *fmt, ...) {
   t_err = buf;
   return s;
 }
+}  // namespace fg
 
-#define CUDA_TRY(expr)                                                                      \
-  do {                                                                                      \
-    cudaError_t e_ = (expr);                                                                \
-    if (e_ != cudaSuccess)                                                                  \
-      return fail(e_ == cudaErrorMemoryAllocation ? FG_ERR_OOM : FG_ERR_CUDA, "%s: %s (%s:%d)", \
-                  #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                       \
-  } while (0)
-
-struct DevBuf {
-  void *p = nullptr;
-  size_t bytes = 0;
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
-  }
-  cudaError_t reserve(size_t b) {
-    if (b <= bytes && p) return cudaSuccess;
-    release();
-    cudaError_t e = cudaMalloc(&p, b ? b : 16);
-    if (e == cudaSuccess) bytes = b;
-    else p = nullptr;
-    return e;
-  }
-  template <typename T>
-  T *as() const { return reinterpret_cast<T *>(p); }
-};
-
-struct Workspace {
-  DevBuf cnt, prio, dirty, cur, pend, qbest, items, iprio, blocksum, e_key, e_op, b_op, ctrl;
-  DevBuf scratch_r, scratch_c, scratch_p, state, io_src, io_out, io_out2;
-  DevBuf pl_dist, pl_rr, pl_pp, pl_cc, pl_stamp, pl_f0, pl_f1, pl_sizes;
-  bool pend_clean = true;
-  void release_all() {
-    DevBuf *all[] = {&cnt, &prio, &dirty, &cur, &pend, &qbest, &items, &iprio, &blocksum, &e_key, &e_op,
-                     &b_op, &ctrl, &scratch_r, &scratch_c, &scratch_p, &state, &io_src, &io_out, &io_out2, &pl_dist, &pl_rr,
-                     &pl_pp, &pl_cc, &pl_stamp, &pl_f0, &pl_f1, &pl_sizes};
-    for (DevBuf *b : all) b->release();
-  }
-};
+namespace {
 
 // A batch whose status fg_sync has not read yet.
 struct Pending {
   cudaStream_t stream;
   fg_graph *graph;
-  Ctrl *host;  // pinned copy of the device control block
+  Workspace *ws;  // workspace the batch ran on (its pending bitmaps need a reset after an abort)
+  Ctrl *host;     // pinned copy of the device control block
   unsigned launches;
 };
 
@@ -101,27 +65,6 @@ Ctrl *take_slot() {
 }
 
 }  // namespace
-
-struct fg_graph {
-  DevGraph dg;
-  int64_t n = 0, m = 0;
-  int method = FG_PART_RANGE, S = 0, slog2 = 0, nparts = 0;
-  int64_t cut = 0;
-  bool weighted = false;
-  int device = 0;
-  DevBuf rp, adj, wt, orig, intl;
-  size_t graph_bytes = 0;
-  std::mutex mu;
-  cudaEvent_t last_done = nullptr;
-  bool has_last = false;
-  Workspace ws;
-  fg_stats_t last_stats{};
-  int engine_blocks = 0, engine_threads = 0;
-  size_t engine_smem = 0;
-  int engine_qtype = -1;
-  uint32_t max_degree = 0;
-  int plain_blocks = 0, plain_threads = 0;
-};
 
 extern "C" void fg_default_opts(fg_opts *o) {
   if (!o) return;
@@ -370,7 +313,10 @@ extern "C" fg_status fg_graph_destroy(fg_graph *g) {
     {
       std::lock_guard<std::mutex> lp(g_pending_mu);
       for (auto &p : g_pending)
-        if (p.graph == g) p.graph = nullptr;
+        if (p.graph == g) {
+          p.graph = nullptr;
+          p.ws = nullptr;
+        }
     }
     g->ws.release_all();
     g->rp.release(); g->adj.release(); g->wt.release(); g->orig.release(); g->intl.release();
@@ -411,9 +357,9 @@ static void merge_opts(const fg_opts *in, fg_opts *o) {
 namespace {
 
 // workspace for a buffered launch of nb queries
-fg_status ensure_engine_ws(fg_graph *g, int qtype, int64_t nb, uint64_t e_cap, bool need_r, int blocks) {
+fg_status ensure_engine_ws(fg_graph *g, Workspace &ws, int qtype, int64_t nb, uint64_t e_cap, bool need_r,
+                           int blocks) {
   const bool relabelled = g->dg.orig != nullptr;
-  Workspace &ws = g->ws;
   const uint64_t K = (uint64_t)g->nparts * (uint64_t)nb;
   const uint64_t nw = (uint64_t)(g->S / 32);
   CUDA_TRY(ws.cnt.reserve(4 * K));
@@ -445,8 +391,7 @@ fg_status ensure_engine_ws(fg_graph *g, int qtype, int64_t nb, uint64_t e_cap, b
   return FG_OK;
 }
 
-fg_status ensure_plain_ws(fg_graph *g, int qtype, int64_t nb, bool need_r) {
-  Workspace &ws = g->ws;
+fg_status ensure_plain_ws(fg_graph *g, Workspace &ws, int qtype, int64_t nb, bool need_r) {
   const size_t n = (size_t)g->n;
   CUDA_TRY(ws.ctrl.reserve(sizeof(Ctrl)));
   CUDA_TRY(ws.pl_stamp.reserve(4 * n));
@@ -465,8 +410,17 @@ fg_status ensure_plain_ws(fg_graph *g, int qtype, int64_t nb, bool need_r) {
   return FG_OK;
 }
 
-fg_status run_batch(fg_graph *g, int qtype, const int32_t *src_in, int32_t nq, uint32_t *dist_in, float alpha,
-                    float eps, float *p_in, float *r_in, double *mass_in, void *stream_v, const fg_opts *opts_in) {
+}  // namespace
+
+namespace fg {
+
+// One batch on workspace ws. shared_ws: ws is the graph's own workspace, so
+// the batch waits for the graph's previous batch (stream order across
+// streams). grid_div > 1 launches the engine on 1/grid_div of the resident
+// grid, so that several batches (server lanes) run side by side.
+fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div, int qtype, const int32_t *src_in,
+                       int32_t nq, uint32_t *dist_in, float alpha, float eps, float *p_in, float *r_in,
+                       double *mass_in, void *stream_v, const fg_opts *opts_in) {
   if (!g) return fail(FG_ERR_INVALID_ARG, "graph is NULL");
   if (nq <= 0) return fail(FG_ERR_INVALID_ARG, "nq must be > 0");
   if (!src_in) return fail(FG_ERR_INVALID_ARG, "src is NULL");
@@ -504,8 +458,7 @@ fg_status run_batch(fg_graph *g, int qtype, const int32_t *src_in, int32_t nq, u
     for (int32_t i = 0; i < nq; ++i)
       if (src_in[i] < 0 || src_in[i] >= n)
         return fail(FG_ERR_INVALID_ARG, "src[%d] = %d out of range", i, src_in[i]);
-    if (g->has_last) CUDA_TRY(cudaEventSynchronize(g->last_done));
-    Workspace &ws = g->ws;
+    if (shared_ws && g->has_last) CUDA_TRY(cudaEventSynchronize(g->last_done));
     const size_t mass_off = ((4 * (size_t)nq + 15) / 16) * 16;
     CUDA_TRY(ws.io_src.reserve(mass_off + 8 * (size_t)nq));
     CUDA_TRY(ws.io_out.reserve(4 * row_elems));
@@ -520,9 +473,7 @@ fg_status run_batch(fg_graph *g, int qtype, const int32_t *src_in, int32_t nq, u
       dist = ws.io_out.as<uint32_t>();
     }
   }
-  if (g->has_last) CUDA_TRY(cudaStreamWaitEvent(stream, g->last_done, 0));
-
-  Workspace &ws = g->ws;
+  if (shared_ws && g->has_last) CUDA_TRY(cudaStreamWaitEvent(stream, g->last_done, 0));
   const bool need_r = (qtype == Q_PPR && rout == nullptr);
   // queries per launch: bounded by the workspace (keys, pending bitmaps, PPR scratch)
   int64_t nb = o.query_batch ? o.query_batch : nq;
@@ -552,7 +503,8 @@ fg_status run_batch(fg_graph *g, int qtype, const int32_t *src_in, int32_t nq, u
       CUDA_TRY(engine_grid_size(qtype, g->S, &g->engine_blocks, &g->engine_threads, &g->engine_smem));
       g->engine_qtype = qtype;
     }
-    fg_status st = ensure_engine_ws(g, qtype, nb, e_cap, need_r, g->engine_blocks);
+    fg_status st = ensure_engine_ws(g, ws, qtype, nb, e_cap, need_r, g->engine_blocks);
+    const int blocks = grid_div > 1 ? std::max(1, g->engine_blocks / grid_div) : g->engine_blocks;
     if (st != FG_OK) return st;
     d_ctrl = ws.ctrl.as<Ctrl>();
     CUDA_TRY(cudaMemsetAsync(d_ctrl, 0, sizeof(Ctrl), stream));
@@ -603,7 +555,7 @@ fg_status run_batch(fg_graph *g, int qtype, const int32_t *src_in, int32_t nq, u
       // lane-per-vertex expansion only on request (measured slower than the
       // warp-shared merge-path on the road-like grid)
       a.lanes = (o.threads_per_vertex == 1 && g->max_degree <= 8) ? 1u : 0u;
-      CUDA_TRY(launch_engine(a, g->engine_blocks, g->engine_threads, g->engine_smem, stream));
+      CUDA_TRY(launch_engine(a, blocks, g->engine_threads, g->engine_smem, stream));
       ++launches;
       if (qtype == Q_PPR) {
         // fold the Kahan terms, mass per query, and (if relabelled) back to original order
@@ -617,7 +569,7 @@ fg_status run_batch(fg_graph *g, int qtype, const int32_t *src_in, int32_t nq, u
       }
     }
   } else {
-    fg_status st = ensure_plain_ws(g, qtype, nb, need_r);
+    fg_status st = ensure_plain_ws(g, ws, qtype, nb, need_r);
     if (st != FG_OK) return st;
     if (g->plain_blocks == 0) CUDA_TRY(plain_grid_size(&g->plain_blocks, &g->plain_threads));
     d_ctrl = ws.ctrl.as<Ctrl>();
@@ -670,8 +622,10 @@ fg_status run_batch(fg_graph *g, int qtype, const int32_t *src_in, int32_t nq, u
       }
     }
   }
-  CUDA_TRY(cudaEventRecord(g->last_done, stream));
-  g->has_last = true;
+  if (shared_ws) {
+    CUDA_TRY(cudaEventRecord(g->last_done, stream));
+    g->has_last = true;
+  }
 
   // status and statistics travel back with the stream
   Ctrl *h = take_slot();
@@ -685,7 +639,7 @@ fg_status run_batch(fg_graph *g, int qtype, const int32_t *src_in, int32_t nq, u
   }
   {
     std::lock_guard<std::mutex> lp(g_pending_mu);
-    g_pending.push_back(Pending{stream, g, h, (unsigned)launches});
+    g_pending.push_back(Pending{stream, g, &ws, h, (unsigned)launches});
   }
   if (host_io) {
     if (qtype == Q_PPR) {
@@ -698,6 +652,17 @@ fg_status run_batch(fg_graph *g, int qtype, const int32_t *src_in, int32_t nq, u
     CUDA_TRY(cudaStreamSynchronize(stream));
   }
   return FG_OK;
+}
+
+}  // namespace fg
+
+namespace {
+
+fg_status run_batch(fg_graph *g, int qtype, const int32_t *src_in, int32_t nq, uint32_t *dist_in, float alpha,
+                    float eps, float *p_in, float *r_in, double *mass_in, void *stream_v, const fg_opts *opts_in) {
+  if (!g) return fail(FG_ERR_INVALID_ARG, "graph is NULL");
+  return run_batch_on(g, g->ws, true, 1, qtype, src_in, nq, dist_in, alpha, eps, p_in, r_in, mass_in, stream_v,
+                      opts_in);
 }
 
 }  // namespace
@@ -749,7 +714,7 @@ extern "C" fg_status fg_sync(void *stream_v) {
       s.max_round_ops = c.max_round_ops;
       for (int k = 0; k < 6; ++k) s.phase_ns[k] = c.phase_ns[k];
       p.graph->last_stats = s;
-      if (c.status != 0 && c.status != FG_ERR_OVERFLOW) p.graph->ws.pend_clean = false;
+      if (c.status != 0 && c.status != FG_ERR_OVERFLOW && p.ws) p.ws->pend_clean = false;
     }
     if (first == FG_OK && c.status != 0) {
       const char *names[] = {"ok", "invalid argument", "out of memory", "CUDA error", "watchdog timeout",

@@ -61,6 +61,22 @@ class fg_stats_t(ctypes.Structure):
         return d
 
 
+FG_QUERY_SSSP, FG_QUERY_BFS, FG_QUERY_PPR = 0, 1, 2
+
+
+class fg_server_opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("lanes", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("full_grid", ctypes.c_int32), ("alpha", ctypes.c_float), ("eps", ctypes.c_float),
+                ("hbm_budget", ctypes.c_int64), ("opts", fg_opts * 3)]
+
+
+class fg_request_info(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("source", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("batch_size", ctypes.c_int32), ("submit_ns", ctypes.c_int64), ("launch_ns", ctypes.c_int64),
+                ("done_ns", ctypes.c_int64), ("result", ctypes.c_void_p), ("residual", ctypes.c_void_p),
+                ("mass", ctypes.c_double)]
+
+
 class fg_graph_info_t(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("partition_vertices", ctypes.c_int32),
                 ("num_partitions", ctypes.c_int32), ("partition_method", ctypes.c_int32),
@@ -69,7 +85,9 @@ class fg_graph_info_t(ctypes.Structure):
 
 EXPORTS = ("fg_default_opts", "fg_default_graph_opts", "fg_graph_create", "fg_graph_create_ex",
            "fg_graph_destroy", "fg_graph_info", "fg_sssp_batch", "fg_bfs_batch", "fg_ppr_batch", "fg_sync",
-           "fg_last_error", "fg_stats", "fg_partition_plan", "fg_sssp_batch_noalloc")
+           "fg_last_error", "fg_stats", "fg_partition_plan", "fg_sssp_batch_noalloc", "fg_default_server_opts",
+           "fg_server_create", "fg_server_destroy", "fg_server_submit", "fg_server_poll", "fg_server_info",
+           "fg_server_release")
 
 FG_NOALLOC_MAX_VERTICES = 1 << 20
 
@@ -104,9 +122,19 @@ def load():
     lib.fg_stats.argtypes = [vp, ctypes.POINTER(fg_stats_t)]
     lib.fg_partition_plan.argtypes = [i64, vp, vp, i32, i32, vp]
     lib.fg_sssp_batch_noalloc.argtypes = [vp, vp, i32, vp, vp]
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    lib.fg_default_server_opts.argtypes = [ctypes.POINTER(fg_server_opts)]
+    lib.fg_default_server_opts.restype = None
+    lib.fg_server_create.argtypes = [vp, ctypes.POINTER(fg_server_opts), ctypes.POINTER(vp)]
+    lib.fg_server_destroy.argtypes = [vp]
+    lib.fg_server_submit.argtypes = [vp, i32, i32, u64p]
+    lib.fg_server_poll.argtypes = [vp, vp, i32, ctypes.POINTER(ctypes.c_int32)]
+    lib.fg_server_info.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(fg_request_info)]
+    lib.fg_server_release.argtypes = [vp, ctypes.c_uint64]
     for name in ("fg_graph_create", "fg_graph_create_ex", "fg_graph_destroy", "fg_graph_info", "fg_sssp_batch",
                  "fg_bfs_batch", "fg_ppr_batch", "fg_sync", "fg_stats", "fg_partition_plan",
-                 "fg_sssp_batch_noalloc"):
+                 "fg_sssp_batch_noalloc", "fg_server_create", "fg_server_destroy", "fg_server_submit",
+                 "fg_server_poll", "fg_server_info", "fg_server_release"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -225,3 +253,47 @@ def fg_partition_plan(n, row_ptr, col, method, partition_vertices, perm_out) -> 
 def fg_sssp_batch_noalloc(g, src, nq, dist_out, stream=None) -> int:
     """Synchronous; device pointers only; graph of at most FG_NOALLOC_MAX_VERTICES vertices."""
     return load().fg_sssp_batch_noalloc(g, _ptr(src), nq, _ptr(dist_out), _stream(stream))
+
+
+def fg_default_server_opts(**overrides) -> fg_server_opts:
+    o = fg_server_opts()
+    load().fg_default_server_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def fg_server_create(g, opts=None):
+    """Returns (status, server handle)."""
+    h = ctypes.c_void_p()
+    st = load().fg_server_create(g, ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
+    return st, h.value
+
+
+def fg_server_destroy(s) -> int:
+    return load().fg_server_destroy(s)
+
+
+def fg_server_submit(s, kind, source):
+    """Returns (status, request id)."""
+    rid = ctypes.c_uint64()
+    st = load().fg_server_submit(s, kind, source, ctypes.byref(rid))
+    return st, rid.value
+
+
+def fg_server_poll(s, cap=1024):
+    """Returns (status, list of completed request ids)."""
+    buf = (ctypes.c_uint64 * max(1, cap))()
+    n = ctypes.c_int32()
+    st = load().fg_server_poll(s, buf, cap, ctypes.byref(n))
+    return st, list(buf[:n.value])
+
+
+def fg_server_info(s, rid):
+    """Returns (status, fg_request_info)."""
+    info = fg_request_info()
+    return load().fg_server_info(s, rid, ctypes.byref(info)), info
+
+
+def fg_server_release(s, rid) -> int:
+    return load().fg_server_release(s, rid)

@@ -39,6 +39,10 @@ def test_struct_sizes_match_header(lib):
     assert o.struct_size == ctypes.sizeof(fg.fg_opts)
     go = fg.fg_default_graph_opts()
     assert go.struct_size == ctypes.sizeof(fg.fg_graph_opts)
+    so = fg.fg_default_server_opts()
+    assert so.struct_size == ctypes.sizeof(fg.fg_server_opts)
+    assert so.lanes == 4 and so.max_batch == 256 and abs(so.alpha - 0.15) < 1e-7
+    assert all(so.opts[k].struct_size == ctypes.sizeof(fg.fg_opts) for k in range(3))
     assert go.partition_method == fg.FG_PART_AUTO and o.mode == fg.FG_MODE_BUFFERED
 
 
@@ -87,6 +91,14 @@ def test_batch_rejects_null_graph(lib):
     assert fg.fg_bfs_batch(None, src, 4, out) == fg.FG_ERR_INVALID_ARG
     assert fg.fg_ppr_batch(None, src, 4, 0.15, 1e-4, out) == fg.FG_ERR_INVALID_ARG
     assert fg.fg_sssp_batch_noalloc(None, src, 4, out) == fg.FG_ERR_INVALID_ARG
+    st, _ = fg.fg_server_create(None, fg.fg_default_server_opts())
+    assert st == fg.FG_ERR_INVALID_ARG
+    st, _ = fg.fg_server_submit(None, fg.FG_QUERY_SSSP, 0)
+    assert st == fg.FG_ERR_INVALID_ARG
+    st, _ = fg.fg_server_poll(None)
+    assert st == fg.FG_ERR_INVALID_ARG
+    assert fg.fg_server_release(None, 1) == fg.FG_ERR_INVALID_ARG
+    assert fg.fg_server_destroy(None) == fg.FG_OK
     st, _ = fg.fg_graph_info(None)
     assert st == fg.FG_ERR_INVALID_ARG
     assert fg.fg_graph_destroy(None) == fg.FG_OK

@@ -1,0 +1,190 @@
+"""Serving loop (fg_server_*): results in a mixed, overlapping stream equal the results alone.
+
+Requests of all three kinds are submitted in waves while earlier batches are
+still on the device. Each SSSP/BFS result must be bit-identical to a batch of
+that one source through fg_sssp_batch / fg_bfs_batch (and to the oracle); each
+PPR result must meet the push bound against the FP64 oracle and agree with its
+stand-alone run within twice that bound (push order may differ), with mass 1.
+"""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2103_14915_gb300 import fg, inputs
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+ALPHA, EPS = 0.15, 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2103_14915_gb300 import build
+    build.build()
+    fg.load()
+    assert torch.cuda.is_available()
+
+
+@pytest.fixture(scope="module")
+def graph():
+    g = inputs.grid(48, 64, 500, 100, seed=21, weights=(100, 10000))
+    go = fg.fg_default_graph_opts(partition_method=fg.FG_PART_GROW, partition_vertices=256)
+    st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, go)
+    fg.check(st)
+    yield g, h
+    fg.fg_graph_destroy(h)
+
+
+def _alone(h, g, kind, s):
+    s_d = torch.tensor([s], dtype=torch.int32, device=DEV)
+    o = fg.fg_default_opts(watchdog_ms=10000)
+    if kind == fg.FG_QUERY_PPR:
+        p = torch.empty((1, g.n), dtype=torch.float32, device=DEV)
+        fg.check(fg.fg_ppr_batch(h, s_d, 1, ALPHA, EPS, p, None, None, None, o))
+        fg.check(fg.fg_sync())
+        return p.cpu().numpy()[0]
+    out = torch.empty((1, g.n), dtype=torch.int32, device=DEV)
+    f = fg.fg_sssp_batch if kind == fg.FG_QUERY_SSSP else fg.fg_bfs_batch
+    fg.check(f(h, s_d, 1, out, None, o))
+    fg.check(fg.fg_sync())
+    return out.cpu().numpy().view(np.uint32)[0]
+
+
+class _DeviceRow:
+    """A server-owned device row seen through __cuda_array_interface__ (no copy, no ownership)."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3}
+
+
+def _row(info, n):
+    ppr = info.kind == fg.FG_QUERY_PPR
+    t = torch.as_tensor(_DeviceRow(info.result, n, "<f4" if ppr else "<i4"), device=DEV).clone()
+    a = t.cpu().numpy()
+    return a if ppr else a.view(np.uint32)
+
+
+def _run_mix(h, g, reqs, lanes, max_batch, waves):
+    so = fg.fg_default_server_opts(lanes=lanes, max_batch=max_batch, alpha=ALPHA, eps=EPS)
+    for k in range(3):
+        so.opts[k].watchdog_ms = 10000
+    st, srv = fg.fg_server_create(h, so)
+    fg.check(st)
+    results, infos = {}, {}
+    try:
+        ids = {}
+        per_wave = (len(reqs) + waves - 1) // waves
+        for w in range(waves):
+            for i, (kind, s) in enumerate(reqs[w * per_wave:(w + 1) * per_wave]):
+                st, rid = fg.fg_server_submit(srv, kind, s)
+                fg.check(st)
+                ids[rid] = w * per_wave + i
+            st, done = fg.fg_server_poll(srv)
+            fg.check(st)
+            for rid in done:
+                st, info = fg.fg_server_info(srv, rid)
+                fg.check(st)
+                results[ids[rid]] = _row(info, g.n)
+                infos[ids[rid]] = (info.status, info.mass, info.batch_size, info.launch_ns, info.done_ns)
+                fg.check(fg.fg_server_release(srv, rid))
+        t_end = time.time() + 60
+        while len(results) < len(reqs):
+            assert time.time() < t_end, "server did not complete the requests"
+            st, done = fg.fg_server_poll(srv)
+            fg.check(st)
+            for rid in done:
+                st, info = fg.fg_server_info(srv, rid)
+                fg.check(st)
+                results[ids[rid]] = _row(info, g.n)
+                infos[ids[rid]] = (info.status, info.mass, info.batch_size, info.launch_ns, info.done_ns)
+                fg.check(fg.fg_server_release(srv, rid))
+        # batches overlapped in time when some launch precedes another's completion
+        spans = sorted((v[3], v[4]) for v in infos.values())
+        overlapped = any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1) if spans[i + 1][0] != spans[i][0])
+    finally:
+        fg.fg_server_destroy(srv)
+    return results, infos, overlapped
+
+
+def test_mix_equals_alone(graph):
+    g, h = graph
+    rng = np.random.default_rng(5)
+    srcs = inputs.sources_uniform(g, 24, seed=31)
+    kinds = rng.integers(0, 3, size=len(srcs))
+    reqs = [(int(k), int(s)) for k, s in zip(kinds, srcs)]
+    reqs.append(reqs[0])  # the same request twice in the mix
+    results, infos, _ = _run_mix(h, g, reqs, lanes=3, max_batch=4, waves=5)
+    deg = np.diff(g.row_ptr).astype(np.float64)
+    for i, (kind, s) in enumerate(reqs):
+        assert infos[i][0] == fg.FG_OK
+        alone = _alone(h, g, kind, s)
+        if kind == fg.FG_QUERY_PPR:
+            pi = oracle.ppr_power(g, [s], ALPHA)[0]
+            bound = EPS * deg + 1e-6
+            assert np.all(np.abs(results[i].astype(np.float64) - pi) <= bound)
+            assert np.all(np.abs(results[i].astype(np.float64) - alone.astype(np.float64)) <= 2 * bound)
+            assert abs(infos[i][1] - 1.0) <= 1e-5
+        else:
+            assert np.array_equal(results[i], alone)
+            ref = oracle.sssp(g, [s])[0] if kind == fg.FG_QUERY_SSSP else oracle.bfs(g, [s])[0]
+            assert np.array_equal(results[i], ref)
+
+
+def test_batches_overlap_on_the_device(graph):
+    g, h = graph
+    srcs = inputs.sources_uniform(g, 48, seed=32)
+    reqs = [(k % 2, int(s)) for k, s in enumerate(srcs)]  # SSSP and BFS
+    results, infos, overlapped = _run_mix(h, g, reqs, lanes=4, max_batch=6, waves=8)
+    assert len(results) == len(reqs)
+    assert max(v[2] for v in infos.values()) > 1  # requests were batched
+    assert overlapped
+    for i, (kind, s) in enumerate(reqs[:6]):
+        assert np.array_equal(results[i], _alone(h, g, kind, s))
+
+
+def test_submit_rejects_bad_requests(graph):
+    g, h = graph
+    st, srv = fg.fg_server_create(h, fg.fg_default_server_opts(lanes=1, max_batch=2))
+    fg.check(st)
+    try:
+        assert fg.fg_server_submit(srv, 7, 0)[0] == fg.FG_ERR_INVALID_ARG
+        assert fg.fg_server_submit(srv, fg.FG_QUERY_BFS, g.n)[0] == fg.FG_ERR_INVALID_ARG
+        st, rid = fg.fg_server_submit(srv, fg.FG_QUERY_BFS, 0)
+        fg.check(st)
+        assert fg.fg_server_release(srv, rid) == fg.FG_ERR_INVALID_ARG  # not completed yet
+        st, info = fg.fg_server_info(srv, rid)
+        assert info.status == -1
+    finally:
+        fg.fg_server_destroy(srv)
+
+
+def test_budget_lowers_batch_size(graph):
+    g, h = graph
+    info = fg.fg_graph_info(h)[1]
+    # device bytes of one PPR request (the most expensive kind) on this relabelled graph:
+    # p and r rows, engine estimate/residual/compensation scratch, per-key buffers
+    per_q = 20 * g.n + info.num_partitions * 36 + g.n / 8
+    so = fg.fg_default_server_opts(lanes=2, max_batch=256, hbm_budget=int(2 * 3 * per_q) + 64)
+    st, srv = fg.fg_server_create(h, so)
+    fg.check(st)
+    try:
+        srcs = inputs.sources_uniform(g, 10, seed=33)
+        for s in srcs:
+            fg.check(fg.fg_server_submit(srv, fg.FG_QUERY_SSSP, int(s))[0])
+        sizes, t_end = [], time.time() + 60
+        while len(sizes) < len(srcs):
+            assert time.time() < t_end
+            st, done = fg.fg_server_poll(srv)
+            fg.check(st)
+            for rid in done:
+                sizes.append(fg.fg_server_info(srv, rid)[1].batch_size)
+                fg.check(fg.fg_server_release(srv, rid))
+        assert max(sizes) == 3  # a full batch of 3 fits each of the 2 lanes, 4 would not
+    finally:
+        fg.fg_server_destroy(srv)
+    st, _ = fg.fg_server_create(h, fg.fg_default_server_opts(lanes=2, hbm_budget=1000))
+    assert st == fg.FG_ERR_OOM

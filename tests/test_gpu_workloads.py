@@ -1,0 +1,106 @@
+"""Parity at the workloads' full sizes, in the launch configuration bench.py times.
+
+The oracle computes sampled rows one by one (Dijkstra, BFS, FP64 power
+iteration); every row is additionally checked against properties that hold at
+any size: the shortest-path / BFS certificate (exact, implementation-free) for
+SSSP and BFS, and for PPR the mass sum(p) + sum(r) = 1, the termination rule
+r(v) < eps * max(d(v), 1) and p, r >= 0.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2103_14915_gb300 import fg, inputs
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2103_14915_gb300 import build
+    build.build()
+    fg.load()
+    assert torch.cuda.is_available()
+
+
+def _graph(g, method, S):
+    go = fg.fg_default_graph_opts(partition_method=method, partition_vertices=S)
+    st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, go)
+    fg.check(st)
+    return h
+
+
+def test_grid1024_bfs_sssp_bench_configuration():
+    import bench
+    name = "grid1024_bfs_sssp"
+    g = inputs.workload_graph(name)
+    srcs = inputs.workload_sources(name, g)
+    assert len(srcs) == bench.NQ == 1024
+    h = _graph(g, fg.FG_PART_GROW, 0)
+    try:
+        s_d = torch.from_numpy(srcs).to(DEV)
+        out = torch.empty((len(srcs), g.n), dtype=torch.int32, device=DEV)
+        rows = [0, 1, 341, 682, 1022, 1023]
+        for kind, tuned in (("bfs", bench.TUNED_BFS), ("sssp", bench.TUNED_SSSP)):
+            f = fg.fg_bfs_batch if kind == "bfs" else fg.fg_sssp_batch
+            fg.check(f(h, s_d, len(srcs), out, None, fg.fg_default_opts(**tuned)))
+            fg.check(fg.fg_sync())
+            got = out.cpu().numpy().view(np.uint32)
+            ref = oracle.bfs(g, srcs[rows]) if kind == "bfs" else oracle.sssp(g, srcs[rows])
+            assert np.array_equal(got[rows], ref)
+            assert oracle.certificate_batch(g, srcs, got, weighted=(kind == "sssp")) == 0
+    finally:
+        fg.fg_graph_destroy(h)
+
+
+def test_rmat22_ppr_full_batch():
+    name = "rmat22_ppr"
+    alpha, eps = 0.15, 1e-7
+    g = inputs.workload_graph(name)
+    srcs = inputs.workload_sources(name, g)
+    assert len(srcs) == 4096
+    h = _graph(g, fg.FG_PART_AUTO, 0)
+    try:
+        nq = len(srcs)
+        s_d = torch.from_numpy(srcs).to(DEV)
+        p = torch.empty((nq, g.n), dtype=torch.float32, device=DEV)
+        r = torch.empty_like(p)
+        mass = torch.empty(nq, dtype=torch.float64, device=DEV)
+        fg.check(fg.fg_ppr_batch(h, s_d, nq, alpha, eps, p, r, mass, None, fg.fg_default_opts()))
+        fg.check(fg.fg_sync())
+        assert float((mass - 1.0).abs().max()) <= 1e-5
+        thr = eps * torch.from_numpy(np.maximum(np.diff(g.row_ptr), 1).astype(np.float32)).to(DEV)
+        for q0 in range(0, nq, 256):
+            assert bool((r[q0:q0 + 256] < thr).all())
+            assert bool((r[q0:q0 + 256] >= 0).all()) and bool((p[q0:q0 + 256] >= 0).all())
+        q = 1234
+        pi = oracle.ppr_power(g, srcs[q:q + 1], alpha)[0]
+        deg = np.diff(g.row_ptr).astype(np.float64)
+        err = np.abs(p[q].cpu().numpy().astype(np.float64) - pi)
+        assert np.all(err <= eps * deg + 1e-6)
+    finally:
+        fg.fg_graph_destroy(h)
+
+
+def test_rmat24_sssp_full_graph_batch():
+    name = "rmat24_sssp"
+    g = inputs.workload_graph(name)
+    srcs = inputs.workload_sources(name, g, k=256)
+    h = _graph(g, fg.FG_PART_AUTO, 0)
+    try:
+        nq = len(srcs)
+        s_d = torch.from_numpy(srcs).to(DEV)
+        out = torch.empty((nq, g.n), dtype=torch.int32, device=DEV)
+        fg.check(fg.fg_sssp_batch(h, s_d, nq, out, None, fg.fg_default_opts(sched=1, sched_window=64)))
+        fg.check(fg.fg_sync())
+        rows = [0, 255]
+        got = out[rows].cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, oracle.sssp(g, srcs[rows]))
+        sample = list(range(0, nq, 16))
+        cert = out[sample].cpu().numpy().view(np.uint32)
+        assert oracle.certificate_batch(g, srcs[sample], cert, weighted=True) == 0
+    finally:
+        fg.fg_graph_destroy(h)
