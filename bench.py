@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the cpu/plain/e2e legs (profiling runs)")
     ap.add_argument("--cpu-sample", type=int, default=512)
     ap.add_argument("--plain-sample", type=int, default=8)
+    ap.add_argument("--serve-lambda", type=float, default=1000.0, help="arrival rate of the serving leg (q/s)")
+    ap.add_argument("--serve-requests", type=int, default=2000, help="requests in the serving leg")
+    ap.add_argument("--serving", action="store_true",
+                    help="only the serving measurement on the directed R-MAT scale-25 graph (mixed SSSP/BFS/PPR)")
+    ap.add_argument("--serve-lambdas", default="2000,5000,10000,20000,50000")
     return ap.parse_args()
 
 
@@ -247,10 +252,40 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_serving(args):
+    """Serving sweep on the directed R-MAT scale-25 graph: one JSON line with p50/p99 per arrival rate."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2103_14915_gb300 import fg, inputs
+    name = "rmat25_serving"
+    g = inputs.workload_graph(name)
+    st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, fg.fg_default_graph_opts())
+    fg.check(st)
+    runs = []
+    try:
+        for lam in [float(x) for x in args.serve_lambdas.split(",") if x]:
+            runs.append(serve_stream(fg, h, g, lam, args.serve_requests, seed=int(lam), lanes=4, max_batch=256,
+                                     kinds=(0, 1, 2), alpha=0.15, eps=1e-6))
+    finally:
+        fg.fg_graph_destroy(h)
+    best = max(r["throughput_qps"] for r in runs)
+    print(json.dumps({"metric": "serving p99 latency", "value": runs[0]["p99_ms"], "unit": "ms", "n_gpus": 1,
+                      "higher_is_better": False, "data": "synthetic",
+                      "config": {"workload": name, "graph": "directed R-MAT scale 25, edge factor 24, weights [1,255]",
+                                 "mix": "1/3 SSSP, 1/3 BFS, 1/3 PPR(alpha=0.15, eps=1e-6)",
+                                 "requests_per_rate": args.serve_requests},
+                      "sustained_qps": best, "runs": runs}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.serving:
+        run_serving(args)
         return
     import torch
     ws, rank, local = dist_env()
@@ -425,6 +460,11 @@ def main():
             result["cpu_baseline"] = {"value": 2 * len(cs) / cdt, "unit": UNIT, "cores": oracle.num_threads(),
                                       "kind": "oracle",
                                       "sample": f"{len(cs)} of the 1,024 sources, BFS + SSSP, OpenMP over queries"}
+            # serving loop on the same resident graph: Poisson stream of mixed requests
+            result["serving"] = dict(
+                serve_stream(fg, h, g, args.serve_lambda, args.serve_requests, seed=77, lanes=4, max_batch=128,
+                             kinds=(0, 1, 2), alpha=0.15, eps=1e-6, opts={0: TUNED_SSSP, 1: TUNED_BFS}),
+                graph=WORKLOAD, mix="1/3 SSSP, 1/3 BFS, 1/3 PPR(alpha=0.15, eps=1e-6)")
     fg.fg_graph_destroy(h)
     if rank == 0:
         print(json.dumps(result), flush=True)

@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kPlainThreads) plain_kernel(PlainArgs a) {
       a.out_u32[gi] = __ldcg(a.dist + i);
     }
   }
-  edges = warp_sum(edges);
+  // edges is warp-uniform (every lane added each chunk's total)
   if (lane == 0 && edges) atomicAdd(&c->edges, edges);
 }
 
