@@ -70,6 +70,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over all ranks of the default process group (identity without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_rate(queries_per_rank: int, world_size: int, slowest_ms: float) -> float:
+    """Whole-job source queries per second: every rank's queries over the slowest rank's time."""
+    return queries_per_rank * world_size / (slowest_ms / 1000.0)
+
+
 def source_sets(g, rank, nq=NQ):
     from paper_2103_14915_gb300 import inputs
     return [inputs.workload_sources(WORKLOAD, g, NQ, set_index=100 * rank + i)[:nq] for i in range(SOURCE_SETS)]
@@ -358,13 +375,8 @@ def main():
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     elapsed_ms = t_start.elapsed_time(t_end)
-    if ws > 1:
-        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-        elapsed_ms = float(t.item())
-    queries = 2 * nq * args.steps * ws
-    value = queries / (elapsed_ms / 1000.0)
+    elapsed_ms = max_over_ranks(elapsed_ms, dev)
+    value = job_rate(2 * nq * args.steps, ws, elapsed_ms)
     bfs_ms = [e[0].elapsed_time(e[1]) for e in evs]
     sssp_ms = [e[1].elapsed_time(e[2]) for e in evs]
 
