@@ -38,7 +38,7 @@ UNIT = "queries/s"
 SOURCE_SETS = 3
 # Scheduling for this workload (per-query priority windows, i.e. Delta-stepping
 # across partitions; chosen by the sweep recorded in the design notes)
-TUNED_BFS = {"sched": 1, "sched_window": 16}
+TUNED_BFS = {"sched": 1, "sched_window": 24}
 TUNED_SSSP = {"sched": 1, "sched_window": 50000}
 
 
@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--opts-bfs", default="", help="JSON overrides of fg_opts for the BFS batches")
     ap.add_argument("--opts-sssp", default="", help="JSON overrides of fg_opts for the SSSP batches")
     ap.add_argument("--partition-vertices", type=int, default=0)
+    ap.add_argument("--no-tune", action="store_true", help="use the hand-swept schedules instead of fg_tune_opts")
     ap.add_argument("--no-extras", action="store_true", help="skip the cpu/plain/e2e legs (profiling runs)")
     ap.add_argument("--cpu-sample", type=int, default=512)
     ap.add_argument("--plain-sample", type=int, default=8)
@@ -60,6 +61,8 @@ def parse():
     ap.add_argument("--serving", action="store_true",
                     help="only the serving measurement on the directed R-MAT scale-25 graph (mixed SSSP/BFS/PPR)")
     ap.add_argument("--serve-lambdas", default="2000,5000,10000,20000,50000")
+    ap.add_argument("--ablation", action="store_true",
+                    help="only the scheduling / yield / partition-size ablation on the bench workload")
     return ap.parse_args()
 
 
@@ -296,6 +299,78 @@ def run_serving(args):
                       "sustained_qps": best, "runs": runs}), flush=True)
 
 
+def run_ablation(args):
+    """Scheduling / yield / partition-size ablation on the bench workload (GPU form of Tab. 4, Fig. 7, Fig. 11).
+
+    One JSON line: for each configuration, the batch time of BFS and SSSP over
+    the first source set and the engine counters (rounds, visits, arcs scanned,
+    operations), all results checked against the first configuration's.
+    """
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda:0")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2103_14915_gb300 import fg, inputs
+    g = inputs.workload_graph(WORKLOAD)
+    nq = args.nq
+    src = torch.from_numpy(source_sets(g, 0, nq)[0]).to(dev)
+    mu_arcs = None
+    rows = []
+
+    def run(h, kind, opts):
+        out = torch.empty((nq, g.n), dtype=torch.int32, device=dev)
+        f = fg.fg_bfs_batch if kind == "bfs" else fg.fg_sssp_batch
+        fg.check(f(h, src, nq, out, None, fg.fg_default_opts(**opts)))
+        fg.check(fg.fg_sync())
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fg.check(f(h, src, nq, out, None, fg.fg_default_opts(**opts)))
+        b.record()
+        fg.check(fg.fg_sync())
+        torch.cuda.synchronize()
+        st, stats = fg.fg_stats(h)
+        d = stats.as_dict()
+        return a.elapsed_time(b), d, out
+
+    ref = {}
+    for S in (256, 512, 1024, 2048):
+        st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0,
+                                      fg.fg_default_graph_opts(partition_method=fg.FG_PART_GROW,
+                                                               partition_vertices=S))
+        fg.check(st)
+        info = fg.fg_graph_info(h)[1]
+        mu = g.m // max(1, info.num_partitions) // nq  # arcs per partition per query (yield heuristic 1 unit)
+        cfgs = [("fifo", {}, {}),
+                ("priority-window", TUNED_BFS, TUNED_SSSP)]
+        if S == 1024:
+            cfgs += [("priority-window/2", {"sched": 1, "sched_window": TUNED_BFS["sched_window"] // 2},
+                      {"sched": 1, "sched_window": TUNED_SSSP["sched_window"] // 2}),
+                     ("priority-window*2", {"sched": 1, "sched_window": TUNED_BFS["sched_window"] * 2},
+                      {"sched": 1, "sched_window": TUNED_SSSP["sched_window"] * 2}),
+                     ("delta-yield (heuristic 2)", {"delta": 8}, {"delta": 20000}),
+                     ("edge-budget 4*mu (heuristic 1)", dict(TUNED_BFS, yield_edges=max(1, 4 * mu)),
+                      dict(TUNED_SSSP, yield_edges=max(1, 4 * mu))),
+                     ("edge-budget 64*mu (heuristic 1)", dict(TUNED_BFS, yield_edges=max(1, 64 * mu)),
+                      dict(TUNED_SSSP, yield_edges=max(1, 64 * mu))),
+                     ("lane-per-vertex expansion", dict(TUNED_BFS, threads_per_vertex=1),
+                      dict(TUNED_SSSP, threads_per_vertex=1))]
+        for name, ob, os_ in cfgs:
+            row = {"S": S, "config": name, "cut_arcs": int(info.cut_arcs)}
+            for kind, o in (("bfs", ob), ("sssp", os_)):
+                ms, d, out = run(h, kind, o)
+                key = kind
+                if key not in ref:
+                    ref[key] = out.cpu()
+                exact = bool(torch.equal(out.cpu(), ref[key]))
+                row[kind] = {"ms": round(ms, 2), "opts": o, "rounds": d["rounds"], "visits": d["visits"],
+                             "arcs": d["edges"], "ops": d["ops"], "same_result": exact}
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+        fg.fg_graph_destroy(h)
+    print(json.dumps({"metric": "ablation", "workload": WORKLOAD, "sources": nq, "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -303,6 +378,9 @@ def main():
         return
     if args.serving:
         run_serving(args)
+        return
+    if args.ablation:
+        run_ablation(args)
         return
     import torch
     ws, rank, local = dist_env()
@@ -328,12 +406,27 @@ def main():
     fg.check(st)
     st, info = fg.fg_graph_info(h)
     fg.check(st)
-    extra_b = dict(TUNED_BFS, **(json.loads(args.opts_bfs) if args.opts_bfs else {}))
-    extra_s = dict(TUNED_SSSP, **(json.loads(args.opts_sssp) if args.opts_sssp else {}))
-    opts_b = fg.fg_default_opts(**extra_b)
-    opts_s = fg.fg_default_opts(**extra_s)
     stream = torch.cuda.current_stream(dev)
     src_d = [torch.from_numpy(s).to(dev) for s in sets]
+    # schedules: the library's autotuner on the first source set (outside the
+    # timed region), or the hand-swept constants with --no-tune
+    tune = {}
+    if args.no_tune:
+        base_b, base_s = dict(TUNED_BFS), dict(TUNED_SSSP)
+    else:
+        keys = ("sched", "sched_window", "threads_per_vertex")
+        picked = []
+        for kind in (fg.FG_QUERY_BFS, fg.FG_QUERY_SSSP):
+            st, best, rep = fg.fg_tune_opts(h, kind, src_d[0], nq, stream)
+            fg.check(st)
+            picked.append({k: int(getattr(best, k)) for k in keys})
+            tune["bfs" if kind == fg.FG_QUERY_BFS else "sssp"] = {
+                "candidates": rep.candidates, "best_ms": rep.best_ms, "default_ms": rep.default_ms}
+        base_b, base_s = picked
+    extra_b = dict(base_b, **(json.loads(args.opts_bfs) if args.opts_bfs else {}))
+    extra_s = dict(base_s, **(json.loads(args.opts_sssp) if args.opts_sssp else {}))
+    opts_b = fg.fg_default_opts(**extra_b)
+    opts_s = fg.fg_default_opts(**extra_s)
     level = torch.empty((nq, g.n), dtype=torch.int32, device=dev)
     dist_t = torch.empty((nq, g.n), dtype=torch.int32, device=dev)
 
@@ -410,7 +503,8 @@ def main():
                    "queries_per_step": 2 * nq, "source_sets": SOURCE_SETS,
                    "partition": {"method": "grow", "S": int(info.partition_vertices),
                                  "parts": int(info.num_partitions), "cut_arcs": int(info.cut_arcs)},
-                   "opts": {"bfs": extra_b, "sssp": extra_s},
+                   "opts": {"bfs": extra_b, "sssp": extra_s, "chosen_by": "hand sweep" if args.no_tune else
+                            "fg_tune_opts on source set 0", "tuner": tune},
                    "l2": f"inputs larger than L2: each step writes {8 * nq * g.n / 1e9:.1f} GB of query state",
                    "parallelism": f"queries sharded over {ws} GPU(s)"},
         "gteps": gteps,
@@ -475,7 +569,7 @@ def main():
             # serving loop on the same resident graph: Poisson stream of mixed requests
             result["serving"] = dict(
                 serve_stream(fg, h, g, args.serve_lambda, args.serve_requests, seed=77, lanes=4, max_batch=128,
-                             kinds=(0, 1, 2), alpha=0.15, eps=1e-6, opts={0: TUNED_SSSP, 1: TUNED_BFS}),
+                             kinds=(0, 1, 2), alpha=0.15, eps=1e-6, opts={0: extra_s, 1: extra_b}),
                 graph=WORKLOAD, mix="1/3 SSSP, 1/3 BFS, 1/3 PPR(alpha=0.15, eps=1e-6)")
     fg.fg_graph_destroy(h)
     if rank == 0:

@@ -86,8 +86,10 @@ typedef struct {
                                visit before yielding. 0 = no limit */
     uint32_t max_rounds;    /* watchdog: rounds before FG_ERR_TIMEOUT. 0 = 1,000,000 */
     uint32_t watchdog_ms;   /* watchdog: longest wait at a device-wide barrier. 0 = 30,000 */
-    uint64_t emit_capacity; /* operations one round may buffer; beyond it, work spills to
-                               per-partition pending bitmaps (lossless). 0 = automatic */
+    uint64_t emit_capacity; /* operations one round may buffer (20 B each). Visits stop once 3/4
+                               of it is reserved; beyond it, work spills to per-partition pending
+                               bitmaps (lossless). 0 = automatic: 128 per (partition, query)
+                               buffer, clamped to [2^22, 2^29] */
     int32_t host_io;        /* 1: src and outputs are HOST pointers; the call copies them and
                                completes before returning (fg_sync still reports status) */
     int32_t query_batch;    /* queries per device launch; 0 = all (bounded by workspace) */
@@ -192,6 +194,32 @@ fg_status fg_stats(const fg_graph *g, fg_stats_t *out);
 fg_status fg_partition_plan(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t method,
                             int32_t partition_vertices, int32_t *perm);
 
+/* query kinds of the autotuner and the serving loop */
+enum { FG_QUERY_SSSP = 0, FG_QUERY_BFS = 1, FG_QUERY_PPR = 2 };
+
+/*
+ * Schedule autotuner. The paper tunes its scheduling and yield parameters by
+ * hand per graph (Sec. 5, Tab. 4); here the host times candidate fg_opts for
+ * one query kind (FG_QUERY_*, declared below) on a sample batch and writes the
+ * fastest to *best: the default (FIFO), then FG_SCHED_PRIORITY windows from
+ * wide to narrow -- multiples of the graph's mean arc weight for SSSP, levels
+ * for BFS -- until two in a row are slower than the best, then, on graphs with
+ * out-degree <= 8, lane-per-vertex expansion with the best window. PPR keeps
+ * the default. src: DEVICE int32[nq] (the sample; a few hundred sources is
+ * typical). The tuner allocates nq * n * 4 B of output rows for the duration
+ * of the call and runs each candidate once on `stream` (it synchronises).
+ * report (nullable) receives the number of candidates and the default's and
+ * the chosen schedule's batch times.
+ */
+typedef struct {
+    int32_t candidates;
+    float best_ms;
+    float default_ms;
+} fg_tune_report;
+
+fg_status fg_tune_opts(fg_graph *g, int32_t kind, const int32_t *src, int32_t nq, void *stream,
+                       fg_opts *best, fg_tune_report *report);
+
 /*
  * Serving loop (continuous batching). Requests -- one SSSP, BFS or PPR query
  * from one source -- are submitted one at a time; fg_server_poll launches
@@ -210,8 +238,6 @@ fg_status fg_partition_plan(int64_t n, const int64_t *row_ptr, const int32_t *co
  * thread.
  */
 typedef struct fg_server fg_server;
-
-enum { FG_QUERY_SSSP = 0, FG_QUERY_BFS = 1, FG_QUERY_PPR = 2 };
 
 typedef struct {
     uint32_t struct_size;   /* sizeof(fg_server_opts) */

@@ -77,6 +77,7 @@ struct fg_graph {
   size_t engine_smem = 0;
   int engine_qtype = -1;
   uint32_t max_degree = 0;
+  double mean_weight = 1.0;        // mean arc weight (1 when unweighted)
   int plain_blocks = 0, plain_threads = 0;
 };
 

@@ -277,6 +277,9 @@ extern "C" fg_status fg_graph_create_ex(int64_t n, int64_t m, const int64_t *row
     CUDA_TRY_G(cudaMemset(g->wt.p, 0, sizeof(uint32_t) * arc_elems));
     if (m > 0) CUDA_TRY_G(cudaMemcpy(g->wt.p, i_wt.data(), sizeof(uint32_t) * (size_t)m, cudaMemcpyHostToDevice));
     g->graph_bytes += sizeof(uint32_t) * (size_t)m;
+    double sum = 0.0;
+    for (int64_t e = 0; e < m; ++e) sum += (double)i_wt[(size_t)e];
+    if (m > 0) g->mean_weight = sum / (double)m;
   }
   for (int64_t v = 0; v < n; ++v) g->max_degree = std::max(g->max_degree, i_rp[(size_t)v + 1] - i_rp[(size_t)v]);
   if (!identity) {
@@ -494,10 +497,11 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
 
   if (o.mode == FG_MODE_BUFFERED) {
     const uint64_t K = (uint64_t)g->nparts * (uint64_t)nb;
-    // the arena holds every seed operation of a launch; beyond that a round's
-    // overflow spills losslessly into the pending bitmaps
+    // the arena holds every seed operation of a launch; beyond that a round
+    // stops at 3/4 of it (arena pressure) and overflow spills losslessly into
+    // the pending bitmaps. 128 slots per key (up to 2^29 slots, 20 B each)
     uint64_t e_cap = o.emit_capacity ? o.emit_capacity
-                                     : std::min<uint64_t>(1ull << 28, std::max<uint64_t>(1ull << 22, 64 * K));
+                                     : std::min<uint64_t>(1ull << 29, std::max<uint64_t>(1ull << 22, 128 * K));
     e_cap = std::min<uint64_t>(std::max<uint64_t>(e_cap, (uint64_t)nb), 1ull << 31);
     if (g->engine_qtype != qtype) {
       CUDA_TRY(engine_grid_size(qtype, g->S, &g->engine_blocks, &g->engine_threads, &g->engine_smem));

@@ -1,0 +1,122 @@
+// Schedule autotuner: times candidate fg_opts for one query kind on a sample
+// batch and keeps the fastest. The window of FG_SCHED_PRIORITY is the knob
+// that matters most and its best value differs by orders of magnitude between
+// graph families (a few weight units on a low-diameter R-MAT graph, ten mean
+// weights on a road-like grid), so candidates are scaled by the graph's mean
+// arc weight (SSSP) or counted in levels (BFS) and tried from the widest
+// window down until two in a row are slower than the best. On graphs with
+// out-degree <= 8 the lane-per-vertex expansion is tried with the best window.
+#include <cstring>
+#include <vector>
+
+#include "fg_host.h"
+
+using namespace fg;
+
+namespace {
+
+fg_status time_batch(fg_graph *g, int kind, const int32_t *src, int32_t nq, void *dst, float *p, void *stream,
+                     const fg_opts &o, cudaEvent_t a, cudaEvent_t b, float *ms) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CUDA_TRY(cudaEventRecord(a, s));
+  fg_status st;
+  if (kind == FG_QUERY_PPR)
+    st = fg_ppr_batch(g, src, nq, 0.15f, 1e-6f, p, nullptr, nullptr, stream, &o);
+  else if (kind == FG_QUERY_BFS)
+    st = fg_bfs_batch(g, src, nq, static_cast<uint32_t *>(dst), stream, &o);
+  else
+    st = fg_sssp_batch(g, src, nq, static_cast<uint32_t *>(dst), stream, &o);
+  if (st != FG_OK) return st;
+  CUDA_TRY(cudaEventRecord(b, s));
+  st = fg_sync(stream);
+  if (st != FG_OK) return st;
+  CUDA_TRY(cudaEventElapsedTime(ms, a, b));
+  return FG_OK;
+}
+
+}  // namespace
+
+extern "C" fg_status fg_tune_opts(fg_graph *g, int32_t kind, const int32_t *src, int32_t nq, void *stream,
+                                  fg_opts *best, fg_tune_report *report) {
+  if (!g || !src || !best) return fail(FG_ERR_INVALID_ARG, "NULL argument");
+  if (nq <= 0) return fail(FG_ERR_INVALID_ARG, "nq must be > 0");
+  if (kind < FG_QUERY_SSSP || kind > FG_QUERY_PPR) return fail(FG_ERR_INVALID_ARG, "unknown query kind %d", kind);
+  CUDA_TRY(cudaSetDevice(g->device));
+  DevBuf out;
+  CUDA_TRY(out.reserve(4 * (size_t)nq * (size_t)g->n));
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  CUDA_TRY(cudaEventCreate(&ea));
+  CUDA_TRY(cudaEventCreate(&eb));
+  struct Guard {
+    cudaEvent_t a, b;
+    DevBuf *o;
+    ~Guard() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      o->release();
+    }
+  } guard{ea, eb, &out};
+
+  fg_opts base;
+  fg_default_opts(&base);
+  float ms = 0.f;
+  int tried = 0;
+  // one untimed run loads the kernels and sizes the workspace
+  fg_status st = time_batch(g, kind, src, nq, out.p, out.as<float>(), stream, base, ea, eb, &ms);
+  if (st != FG_OK) return st;
+  st = time_batch(g, kind, src, nq, out.p, out.as<float>(), stream, base, ea, eb, &ms);
+  if (st != FG_OK) return st;
+  ++tried;
+  fg_opts pick = base;
+  float pick_ms = ms;
+  const float base_ms = ms;
+
+  if (kind != FG_QUERY_PPR) {  // PPR buffers are scheduled first-in first-out
+    std::vector<double> windows;
+    if (kind == FG_QUERY_BFS || !g->weighted) {
+      const double lv[] = {64, 48, 32, 24, 16, 12, 8, 4, 2};
+      windows.assign(lv, lv + sizeof(lv) / sizeof(lv[0]));
+    } else {
+      const double f[] = {16, 10, 6, 4, 2, 1, 0.5, 0.25, 0.125, 1.0 / 16, 1.0 / 32, 1.0 / 64, 1.0 / 128};
+      for (double x : f) windows.push_back(x * g->mean_weight);
+    }
+    int worse = 0;
+    uint32_t last = 0;
+    for (double wd : windows) {
+      const uint32_t w = (uint32_t)(wd < 1.0 ? 1.0 : wd + 0.5);
+      if (w == last) continue;
+      last = w;
+      fg_opts o = base;
+      o.sched = FG_SCHED_PRIORITY;
+      o.sched_window = w;
+      st = time_batch(g, kind, src, nq, out.p, nullptr, stream, o, ea, eb, &ms);
+      if (st != FG_OK) return st;
+      ++tried;
+      if (ms < pick_ms) {
+        pick = o;
+        pick_ms = ms;
+        worse = 0;
+      } else if (pick.sched == FG_SCHED_PRIORITY && ++worse == 2) {
+        break;
+      }
+    }
+    if (g->max_degree <= 8) {
+      fg_opts o = pick;
+      o.threads_per_vertex = 1;
+      st = time_batch(g, kind, src, nq, out.p, nullptr, stream, o, ea, eb, &ms);
+      if (st != FG_OK) return st;
+      ++tried;
+      if (ms < pick_ms) {
+        pick = o;
+        pick_ms = ms;
+      }
+    }
+  }
+  *best = pick;
+  if (report) {
+    report->candidates = tried;
+    report->best_ms = pick_ms;
+    report->default_ms = base_ms;
+  }
+  return FG_OK;
+}

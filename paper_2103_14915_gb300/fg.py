@@ -64,6 +64,10 @@ class fg_stats_t(ctypes.Structure):
 FG_QUERY_SSSP, FG_QUERY_BFS, FG_QUERY_PPR = 0, 1, 2
 
 
+class fg_tune_report(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_int32), ("best_ms", ctypes.c_float), ("default_ms", ctypes.c_float)]
+
+
 class fg_server_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("lanes", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("full_grid", ctypes.c_int32), ("alpha", ctypes.c_float), ("eps", ctypes.c_float),
@@ -87,7 +91,7 @@ EXPORTS = ("fg_default_opts", "fg_default_graph_opts", "fg_graph_create", "fg_gr
            "fg_graph_destroy", "fg_graph_info", "fg_sssp_batch", "fg_bfs_batch", "fg_ppr_batch", "fg_sync",
            "fg_last_error", "fg_stats", "fg_partition_plan", "fg_sssp_batch_noalloc", "fg_default_server_opts",
            "fg_server_create", "fg_server_destroy", "fg_server_submit", "fg_server_poll", "fg_server_info",
-           "fg_server_release")
+           "fg_server_release", "fg_tune_opts")
 
 FG_NOALLOC_MAX_VERTICES = 1 << 20
 
@@ -122,6 +126,7 @@ def load():
     lib.fg_stats.argtypes = [vp, ctypes.POINTER(fg_stats_t)]
     lib.fg_partition_plan.argtypes = [i64, vp, vp, i32, i32, vp]
     lib.fg_sssp_batch_noalloc.argtypes = [vp, vp, i32, vp, vp]
+    lib.fg_tune_opts.argtypes = [vp, i32, vp, i32, vp, ctypes.POINTER(fg_opts), ctypes.POINTER(fg_tune_report)]
     u64p = ctypes.POINTER(ctypes.c_uint64)
     lib.fg_default_server_opts.argtypes = [ctypes.POINTER(fg_server_opts)]
     lib.fg_default_server_opts.restype = None
@@ -134,7 +139,7 @@ def load():
     for name in ("fg_graph_create", "fg_graph_create_ex", "fg_graph_destroy", "fg_graph_info", "fg_sssp_batch",
                  "fg_bfs_batch", "fg_ppr_batch", "fg_sync", "fg_stats", "fg_partition_plan",
                  "fg_sssp_batch_noalloc", "fg_server_create", "fg_server_destroy", "fg_server_submit",
-                 "fg_server_poll", "fg_server_info", "fg_server_release"):
+                 "fg_server_poll", "fg_server_info", "fg_server_release", "fg_tune_opts"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -297,3 +302,11 @@ def fg_server_info(s, rid):
 
 def fg_server_release(s, rid) -> int:
     return load().fg_server_release(s, rid)
+
+
+def fg_tune_opts(g, kind, src, nq, stream=None):
+    """Returns (status, best fg_opts, fg_tune_report)."""
+    best = fg_opts()
+    rep = fg_tune_report()
+    st = load().fg_tune_opts(g, kind, _ptr(src), nq, _stream(stream), ctypes.byref(best), ctypes.byref(rep))
+    return st, best, rep

@@ -99,6 +99,8 @@ def test_batch_rejects_null_graph(lib):
     assert st == fg.FG_ERR_INVALID_ARG
     assert fg.fg_server_release(None, 1) == fg.FG_ERR_INVALID_ARG
     assert fg.fg_server_destroy(None) == fg.FG_OK
+    st, _, _ = fg.fg_tune_opts(None, fg.FG_QUERY_SSSP, src, 4)
+    assert st == fg.FG_ERR_INVALID_ARG
     st, _ = fg.fg_graph_info(None)
     assert st == fg.FG_ERR_INVALID_ARG
     assert fg.fg_graph_destroy(None) == fg.FG_OK

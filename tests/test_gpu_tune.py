@@ -1,0 +1,48 @@
+"""Schedule autotuner (fg_tune_opts): picks a schedule at least as fast as the default, and the
+schedule it picks computes the same exact distances."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2103_14915_gb300 import fg, inputs
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2103_14915_gb300 import build
+    build.build()
+    fg.load()
+    assert torch.cuda.is_available()
+
+
+@pytest.mark.parametrize("make,method,S", [
+    (lambda: inputs.grid(96, 96, 500, 100, seed=7, weights=(100, 10000)), fg.FG_PART_GROW, 256),
+    (lambda: inputs.rmat(12, 16, seed=9, weights=(1, 255)), fg.FG_PART_RANGE, 256),
+], ids=["grid", "rmat"])
+@pytest.mark.parametrize("kind", [fg.FG_QUERY_SSSP, fg.FG_QUERY_BFS])
+def test_tuned_schedule_is_exact_and_not_slower(make, method, S, kind):
+    g = make()
+    go = fg.fg_default_graph_opts(partition_method=method, partition_vertices=S)
+    st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, go)
+    fg.check(st)
+    try:
+        srcs = inputs.sources_uniform(g, 64, seed=3)
+        s_d = torch.from_numpy(srcs).to(DEV)
+        st, best, rep = fg.fg_tune_opts(h, kind, s_d, len(srcs))
+        fg.check(st)
+        assert rep.candidates >= 2 and rep.best_ms <= rep.default_ms
+        assert best.struct_size == fg.fg_default_opts().struct_size
+        out = torch.empty((len(srcs), g.n), dtype=torch.int32, device=DEV)
+        f = fg.fg_sssp_batch if kind == fg.FG_QUERY_SSSP else fg.fg_bfs_batch
+        fg.check(f(h, s_d, len(srcs), out, None, best))
+        fg.check(fg.fg_sync())
+        rows = [0, 63]
+        ref = oracle.sssp(g, srcs[rows]) if kind == fg.FG_QUERY_SSSP else oracle.bfs(g, srcs[rows])
+        assert np.array_equal(out.cpu().numpy().view(np.uint32)[rows], ref)
+    finally:
+        fg.fg_graph_destroy(h)

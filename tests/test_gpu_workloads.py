@@ -44,9 +44,14 @@ def test_grid1024_bfs_sssp_bench_configuration():
         s_d = torch.from_numpy(srcs).to(DEV)
         out = torch.empty((len(srcs), g.n), dtype=torch.int32, device=DEV)
         rows = [0, 1, 341, 682, 1022, 1023]
-        for kind, tuned in (("bfs", bench.TUNED_BFS), ("sssp", bench.TUNED_SSSP)):
+        # bench.py takes its schedules from the autotuner on this source set
+        st, tb, _ = fg.fg_tune_opts(h, fg.FG_QUERY_BFS, s_d, len(srcs))
+        fg.check(st)
+        st, ts, _ = fg.fg_tune_opts(h, fg.FG_QUERY_SSSP, s_d, len(srcs))
+        fg.check(st)
+        for kind, tuned in (("bfs", tb), ("sssp", ts)):
             f = fg.fg_bfs_batch if kind == "bfs" else fg.fg_sssp_batch
-            fg.check(f(h, s_d, len(srcs), out, None, fg.fg_default_opts(**tuned)))
+            fg.check(f(h, s_d, len(srcs), out, None, tuned))
             fg.check(fg.fg_sync())
             got = out.cpu().numpy().view(np.uint32)
             ref = oracle.bfs(g, srcs[rows]) if kind == "bfs" else oracle.sssp(g, srcs[rows])
@@ -94,7 +99,7 @@ def test_rmat24_sssp_full_graph_batch():
         nq = len(srcs)
         s_d = torch.from_numpy(srcs).to(DEV)
         out = torch.empty((nq, g.n), dtype=torch.int32, device=DEV)
-        fg.check(fg.fg_sssp_batch(h, s_d, nq, out, None, fg.fg_default_opts(sched=1, sched_window=64)))
+        fg.check(fg.fg_sssp_batch(h, s_d, nq, out, None, fg.fg_default_opts(sched=1, sched_window=4)))
         fg.check(fg.fg_sync())
         rows = [0, 255]
         got = out[rows].cpu().numpy().view(np.uint32)
