@@ -285,9 +285,16 @@ def run_serving(args):
     fg.check(st)
     runs = []
     try:
+        # schedules for this graph from the autotuner on a 64-source sample
+        sample = torch.from_numpy(inputs.sources_uniform(g, 64, 4242)).to("cuda:0")
+        opts = {}
+        for kind in (fg.FG_QUERY_SSSP, fg.FG_QUERY_BFS):
+            st, best, _ = fg.fg_tune_opts(h, kind, sample, 64)
+            fg.check(st)
+            opts[kind] = {k: int(getattr(best, k)) for k in ("sched", "sched_window", "delta", "threads_per_vertex")}
         for lam in [float(x) for x in args.serve_lambdas.split(",") if x]:
             runs.append(serve_stream(fg, h, g, lam, args.serve_requests, seed=int(lam), lanes=4, max_batch=256,
-                                     kinds=(0, 1, 2), alpha=0.15, eps=1e-6))
+                                     kinds=(0, 1, 2), alpha=0.15, eps=1e-6, opts=opts))
     finally:
         fg.fg_graph_destroy(h)
     best = max(r["throughput_qps"] for r in runs)
@@ -296,7 +303,7 @@ def run_serving(args):
                       "config": {"workload": name, "graph": "directed R-MAT scale 25, edge factor 24, weights [1,255]",
                                  "mix": "1/3 SSSP, 1/3 BFS, 1/3 PPR(alpha=0.15, eps=1e-6)",
                                  "requests_per_rate": args.serve_requests},
-                      "sustained_qps": best, "runs": runs}), flush=True)
+                      "sustained_qps": best, "opts": {"sssp": opts[0], "bfs": opts[1]}, "runs": runs}), flush=True)
 
 
 def run_ablation(args):
@@ -414,7 +421,7 @@ def main():
     if args.no_tune:
         base_b, base_s = dict(TUNED_BFS), dict(TUNED_SSSP)
     else:
-        keys = ("sched", "sched_window", "threads_per_vertex")
+        keys = ("sched", "sched_window", "delta", "threads_per_vertex")
         picked = []
         for kind in (fg.FG_QUERY_BFS, fg.FG_QUERY_SSSP):
             st, best, rep = fg.fg_tune_opts(h, kind, src_d[0], nq, stream)

@@ -203,8 +203,9 @@ enum { FG_QUERY_SSSP = 0, FG_QUERY_BFS = 1, FG_QUERY_PPR = 2 };
  * one query kind (FG_QUERY_*, declared below) on a sample batch and writes the
  * fastest to *best: the default (FIFO), then FG_SCHED_PRIORITY windows from
  * wide to narrow -- multiples of the graph's mean arc weight for SSSP, levels
- * for BFS -- until two in a row are slower than the best, then, on graphs with
- * out-degree <= 8, lane-per-vertex expansion with the best window. PPR keeps
+ * for BFS -- until one takes more than twice the best time, then delta (yield
+ * heuristic 2) of half and a quarter of the best window, then, on graphs with
+ * out-degree <= 8, lane-per-vertex expansion. PPR keeps
  * the default. src: DEVICE int32[nq] (the sample; a few hundred sources is
  * typical). The tuner allocates nq * n * 4 B of output rows for the duration
  * of the call and runs each candidate once on `stream` (it synchronises).

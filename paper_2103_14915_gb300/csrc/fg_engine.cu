@@ -253,20 +253,11 @@ __device__ __forceinline__ void store_slice(uint32_t *dst, const uint32_t *src, 
   }
 }
 
-// CSR view of the resident partition. rp is indexed by the local vertex id and
-// holds absolute arc offsets; adj / wt are indexed by (arc - off).
-struct PartView {
-  const uint32_t *rp;
-  const uint32_t *adj;
-  const uint32_t *wt;
-  uint32_t off;
-  uint32_t narc;  // arcs addressable through adj/wt: [off, off + narc)
-  uint32_t part;  // partition this view belongs to
-};
-
-// A vertex's arc range must lie inside the view (never index outside it).
-__device__ __forceinline__ bool arcs_in_view(const PartView &pv, uint32_t e0, uint32_t deg) {
-  return e0 >= pv.off && (uint64_t)(e0 - pv.off) + deg <= (uint64_t)pv.narc;
+// The resident partition's CSR: prp = rp + partition base, indexed by the
+// local vertex id, holding absolute arc offsets into g.adj / g.wt.
+// A vertex's arc range must lie inside the arc arrays (never index outside them).
+__device__ __forceinline__ bool arcs_in_range(const DevGraph &g, uint32_t e0, uint32_t deg) {
+  return (uint64_t)e0 + deg <= g.m;
 }
 
 __device__ __forceinline__ uint32_t relax_value(const EngineArgs &a, uint32_t d, uint32_t w) {
@@ -303,7 +294,7 @@ __device__ __forceinline__ void relax_local(const WarpSmem &w, uint32_t lu, uint
 // SSSP / BFS visit of one (partition, query) buffer.
 // ---------------------------------------------------------------------------
 template <int QT, bool LANES>
-__device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, uint32_t qbound, const PartView &pv,
+__device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, uint32_t qbound, const uint32_t *prp,
                            Counters &ctr, ArenaSlots &sl) {
   const DevGraph &g = a.g;
   const int lane = lane_id();
@@ -316,10 +307,6 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
   uint32_t *drow = a.dist + (size_t)q * (size_t)g.n;
   WarpSmem w = w0;
   const WordRange wr(nw, lane);
-  if (pv.part != p) {  // the resident CSR must be this item's partition
-    if (lane == 0) raise_status(a.ctrl, FG_ERR_CUDA, kSiteStage);
-    return;
-  }
 
   // 1. stage the query's slice of this partition (bypassing L1)
   load_slice(w.d, drow + base, Sp, lane);
@@ -450,9 +437,9 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
             b &= b - 1;
             v = (uint32_t)wd * 32u + (uint32_t)t;
             dv = w.d[v];
-            e0 = pv.rp[v];
-            deg = pv.rp[v + 1] - e0;
-            if (deg > (uint32_t)kLaneMaxDeg || !arcs_in_view(pv, e0, deg)) {  // inconsistent view: skip
+            e0 = prp[v];
+            deg = prp[v + 1] - e0;
+            if (deg > (uint32_t)kLaneMaxDeg || !arcs_in_range(g, e0, deg)) {  // inconsistent view: skip
               raise_status(a.ctrl, FG_ERR_CUDA, kSiteDegree);
               deg = 0;
             }
@@ -464,8 +451,8 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
             u[j] = 0u;
             nd[j] = 0u;
             if ((uint32_t)j < deg) {
-              u[j] = pv.adj[e0 - pv.off + j];
-              const uint32_t wgt = (QT == Q_BFS || pv.wt == nullptr) ? 1u : pv.wt[e0 - pv.off + j];
+              u[j] = g.adj[e0 + j];
+              const uint32_t wgt = (QT == Q_BFS || g.wt == nullptr) ? 1u : g.wt[e0 + j];
               nd[j] = relax_value(a, dv, wgt);
             }
           }
@@ -503,9 +490,9 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
         if (idx < F) {
           if (!reg_front) v = frontier_select(w, nw, idx);
           dv = w.d[v];
-          a0 = pv.rp[v];
-          deg = pv.rp[v + 1] - a0;
-          if (deg > g.max_deg || !arcs_in_view(pv, a0, deg)) {  // inconsistent view: skip
+          a0 = prp[v];
+          deg = prp[v + 1] - a0;
+          if (deg > g.max_deg || !arcs_in_range(g, a0, deg)) {  // inconsistent view: skip
             raise_status(a.ctrl, FG_ERR_CUDA, kSiteDegree);
             deg = 0;
           }
@@ -524,8 +511,8 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
           uint32_t u = 0, nd = 0;
           bool ext = false;
           if (has) {
-            u = pv.adj[eL - pv.off];
-            const uint32_t wgt = (QT == Q_BFS || pv.wt == nullptr) ? 1u : pv.wt[eL - pv.off];
+            u = g.adj[eL];
+            const uint32_t wgt = (QT == Q_BFS || g.wt == nullptr) ? 1u : g.wt[eL];
             nd = relax_value(a, du, wgt);
             if ((u >> g.slog2) == p) {
               relax_local(w, u & (uint32_t)(S - 1), nd, T, Ty);
@@ -583,13 +570,13 @@ __device__ void visit_dist(const EngineArgs &a, const WarpSmem &w0, uint4 item, 
 // Residuals of the slice live in shared memory; estimates and their Kahan
 // compensation are updated in global memory (single writer per slice).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float ppr_thr(const PartView &pv, float eps, uint32_t v_local) {
-  const uint32_t d = pv.rp[v_local + 1] - pv.rp[v_local];
+__device__ __forceinline__ float ppr_thr(const uint32_t *prp, float eps, uint32_t v_local) {
+  const uint32_t d = prp[v_local + 1] - prp[v_local];
   return eps * (float)(d > 0u ? d : 1u);
 }
 
 
-__device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, const PartView &pv, Counters &ctr) {
+__device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, const uint32_t *prp, Counters &ctr) {
   const DevGraph &g = a.g;
   const int lane = lane_id();
   const uint32_t key = item.x, off = item.y, cnt = item.z, flags = item.w;
@@ -608,10 +595,6 @@ __device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, c
   const float alpha = a.alpha, eps = a.eps;
   const float beta = 1.0f - alpha;
   const uint32_t src_int = g.intl ? (uint32_t)g.intl[a.src[q]] : (uint32_t)a.src[q];
-  if (pv.part != p) {  // the resident CSR must be this item's partition
-    if (lane == 0) raise_status(a.ctrl, FG_ERR_CUDA, kSiteStage);
-    return;
-  }
 
   load_slice(w.d, reinterpret_cast<const uint32_t *>(rrow + base), Sp, lane);
   for (int i = Sp + lane; i < S; i += 32) rs[i] = 0.f;
@@ -630,7 +613,7 @@ __device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, c
   for (uint32_t j = lane; j < cnt; j += 32) {
     const uint2 o = __ldcg(ops + j);
     const float inc = __uint_as_float(o.y);
-    const float thr = ppr_thr(pv, eps, o.x);
+    const float thr = ppr_thr(prp, eps, o.x);
     const float old = atomicAdd(&rs[o.x], inc);
     if (old < thr && __fadd_rn(old, inc) >= thr) atomicOr(&w.cur[o.x >> 5], 1u << (o.x & 31));
   }
@@ -657,9 +640,9 @@ __device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, c
       uint32_t v = 0, a0 = 0, deg = 0;
       if (valid) {
         v = frontier_select(w, nw, idx);
-        a0 = pv.rp[v];
-        deg = pv.rp[v + 1] - a0;
-        if (deg > g.max_deg || !arcs_in_view(pv, a0, deg)) {  // inconsistent view: skip
+        a0 = prp[v];
+        deg = prp[v + 1] - a0;
+        if (deg > g.max_deg || !arcs_in_range(g, a0, deg)) {  // inconsistent view: skip
           raise_status(a.ctrl, FG_ERR_CUDA, kSiteDegree);
           deg = 0;
         }
@@ -680,7 +663,7 @@ __device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, c
         const uint32_t eL = __shfl_sync(kFull, a0, L) + (t - __shfl_sync(kFull, exd, L));
         bool ext = false;
         if (has) {
-          const uint32_t u = degL > 0u ? pv.adj[eL - pv.off] : src_int;
+          const uint32_t u = degL > 0u ? g.adj[eL] : src_int;
           ext = (u >> g.slog2) != p;
         }
         n_ext += __popc(__ballot_sync(kFull, ext));
@@ -723,10 +706,10 @@ __device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, c
         bool ext = false;
         uint32_t u = 0;
         if (has) {
-          u = degL > 0u ? pv.adj[eL - pv.off] : src_int;
+          u = degL > 0u ? g.adj[eL] : src_int;
           if ((u >> g.slog2) == p) {
             const uint32_t lu = u & (uint32_t)(S - 1);
-            const float thr = ppr_thr(pv, eps, lu);
+            const float thr = ppr_thr(prp, eps, lu);
             const float old = atomicAdd(&rs[lu], inc);
             if (old < thr && __fadd_rn(old, inc) >= thr) atomicOr(&w.nxt[lu >> 5], 1u << (lu & 31));
           } else {
@@ -1106,13 +1089,7 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
         if (idx >= (uint32_t)tot_items) break;
         const uint4 it = __ldcg(a.items + idx);
         const uint32_t p = it.x / (uint32_t)a.nq;
-        PartView pv;
-        pv.rp = a.g.rp + ((size_t)p << a.g.slog2);
-        pv.adj = a.g.adj;
-        pv.wt = a.g.wt;
-        pv.off = 0u;
-        pv.narc = (uint32_t)a.g.m;
-        pv.part = p;
+        const uint32_t *prp = a.g.rp + ((size_t)p << a.g.slog2);
         bool defer = !kPPR && (it.w & 2u);
         if (!kPPR && !defer) {
           unsigned long long cursor = 0;
@@ -1123,13 +1100,13 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
         if (defer) {
           carry_item(a, it, __ldcg(a.iprio + idx));
         } else if (kPPR) {
-          visit_ppr(a, w, it, pv, ctr);
+          visit_ppr(a, w, it, prp, ctr);
         } else {
           const uint32_t q = it.x - p * (uint32_t)a.nq;
           const uint32_t qbound =
               a.sched == FG_SCHED_PRIORITY ? sat_add_u32(__ldcg(qb_cur + q), a.sched_window) : kInf;
-          if (a.lanes) visit_dist<QT, true>(a, w, it, qbound, pv, ctr, sl);
-          else visit_dist<QT, false>(a, w, it, qbound, pv, ctr, sl);
+          if (a.lanes) visit_dist<QT, true>(a, w, it, qbound, prp, ctr, sl);
+          else visit_dist<QT, false>(a, w, it, qbound, prp, ctr, sl);
         }
       }
       release_slots(a, sl);  // before the barrier: SCATTER reads every reserved slot

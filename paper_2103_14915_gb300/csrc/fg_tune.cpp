@@ -4,8 +4,9 @@
 // graph families (a few weight units on a low-diameter R-MAT graph, ten mean
 // weights on a road-like grid), so candidates are scaled by the graph's mean
 // arc weight (SSSP) or counted in levels (BFS) and tried from the widest
-// window down until two in a row are slower than the best. On graphs with
-// out-degree <= 8 the lane-per-vertex expansion is tried with the best window.
+// window down until one takes more than twice the best time; then yield
+// heuristic 2 (delta = half and a quarter of the window) is tried on top. On
+// graphs with out-degree <= 8 the lane-per-vertex expansion is tried last.
 #include <cstring>
 #include <vector>
 
@@ -80,7 +81,6 @@ extern "C" fg_status fg_tune_opts(fg_graph *g, int32_t kind, const int32_t *src,
       const double f[] = {16, 10, 6, 4, 2, 1, 0.5, 0.25, 0.125, 1.0 / 16, 1.0 / 32, 1.0 / 64, 1.0 / 128};
       for (double x : f) windows.push_back(x * g->mean_weight);
     }
-    int worse = 0;
     uint32_t last = 0;
     for (double wd : windows) {
       const uint32_t w = (uint32_t)(wd < 1.0 ? 1.0 : wd + 0.5);
@@ -95,9 +95,25 @@ extern "C" fg_status fg_tune_opts(fg_graph *g, int32_t kind, const int32_t *src,
       if (ms < pick_ms) {
         pick = o;
         pick_ms = ms;
-        worse = 0;
-      } else if (pick.sched == FG_SCHED_PRIORITY && ++worse == 2) {
-        break;
+      } else if (ms > 2.f * pick_ms) {
+        break;  // narrower windows only add rounds from here on
+      }
+    }
+    // yield heuristic 2 on top of the chosen window: values beyond (first value
+    // + delta) wait for a later visit
+    if (pick.sched == FG_SCHED_PRIORITY) {
+      const uint32_t w = pick.sched_window;
+      for (uint32_t dl : {w / 2u, w / 4u}) {
+        if (dl == 0u) continue;
+        fg_opts o = pick;
+        o.delta = dl;
+        st = time_batch(g, kind, src, nq, out.p, nullptr, stream, o, ea, eb, &ms);
+        if (st != FG_OK) return st;
+        ++tried;
+        if (ms < pick_ms) {
+          pick = o;
+          pick_ms = ms;
+        }
       }
     }
     if (g->max_degree <= 8) {
