@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--serving", action="store_true",
                     help="only the serving measurement on the directed R-MAT scale-25 graph (mixed SSSP/BFS/PPR)")
     ap.add_argument("--serve-lambdas", default="2000,5000,10000,20000,50000")
+    ap.add_argument("--configs", action="store_true",
+                    help="only the other workloads (R-MAT s14 plain, s22 PPR, s24 SSSP) with their baselines")
     ap.add_argument("--ablation", action="store_true",
                     help="only the scheduling / yield / partition-size ablation on the bench workload")
     return ap.parse_args()
@@ -378,6 +380,125 @@ def run_ablation(args):
     print(json.dumps({"metric": "ablation", "workload": WORKLOAD, "sources": nq, "rows": rows}), flush=True)
 
 
+def run_configs(args):
+    """The other workloads (R-MAT s14 plain SSSP, R-MAT s22 PPR, R-MAT s24 SSSP): buffered engine,
+    plain per-query GPU form and the CPU oracle on the host cores, one JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda:0")
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    from paper_2103_14915_gb300 import fg, inputs
+    res = {"metric": "other workloads", "n_gpus": 1, "data": "synthetic", "cpu_cores": oracle.num_threads()}
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        fg.check(fg.fg_sync())
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    def graph(name):
+        g = inputs.workload_graph(name)
+        st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, fg.fg_default_graph_opts())
+        fg.check(st)
+        return g, h
+
+    # cfg 1: R-MAT s14, 64 SSSP sources one at a time (plain), and as one buffered batch
+    name = "rmat14_plain_sssp"
+    g, h = graph(name)
+    src = inputs.workload_sources(name, g)
+    s_d = torch.from_numpy(src).to(dev)
+    out = torch.empty((len(src), g.n), dtype=torch.int32, device=dev)
+    fg.check(fg.fg_sssp_batch(h, s_d, len(src), out, None, fg.fg_default_opts(mode=fg.FG_MODE_PLAIN)))
+    fg.check(fg.fg_sync())
+    t_plain = timed(lambda: fg.check(fg.fg_sssp_batch(h, s_d, len(src), out, None,
+                                                      fg.fg_default_opts(mode=fg.FG_MODE_PLAIN))))
+    exact_plain = bool(np.array_equal(out.cpu().numpy().view(np.uint32), oracle.sssp(g, src)))
+    st, ob, _ = fg.fg_tune_opts(h, fg.FG_QUERY_SSSP, s_d, len(src))
+    fg.check(st)
+    t_buf = timed(lambda: fg.check(fg.fg_sssp_batch(h, s_d, len(src), out, None, ob)))
+    t0 = time.perf_counter()
+    ref = oracle.sssp(g, src)
+    t_cpu = time.perf_counter() - t0
+    arcs = sum(oracle.reachable_arcs(g, r) for r in ref)
+    res["rmat14_plain_sssp"] = {
+        "plain_gpu_qps": len(src) / (t_plain / 1e3), "plain_gpu_ms_per_query": t_plain / len(src),
+        "plain_gteps": arcs / (t_plain / 1e3) / 1e9, "buffered_qps": len(src) / (t_buf / 1e3),
+        "cpu_oracle_qps": len(src) / t_cpu, "exact": exact_plain and bool(
+            np.array_equal(out.cpu().numpy().view(np.uint32), ref)), "sources": len(src)}
+    fg.fg_graph_destroy(h)
+
+    # cfg 3: R-MAT s22 PPR, 4,096 log-degree seeds (sub-batched by the library)
+    name = "rmat22_ppr"
+    alpha, eps = 0.15, 1e-7
+    g, h = graph(name)
+    src = inputs.workload_sources(name, g)
+    s_d = torch.from_numpy(src).to(dev)
+    nq = len(src)
+    p = torch.empty((nq, g.n), dtype=torch.float32, device=dev)
+    mass = torch.empty(nq, dtype=torch.float64, device=dev)
+    o = fg.fg_default_opts()
+    fg.check(fg.fg_ppr_batch(h, s_d[:256], 256, alpha, eps, p, None, mass, None, o))
+    fg.check(fg.fg_sync())
+    t_buf = timed(lambda: fg.check(fg.fg_ppr_batch(h, s_d, nq, alpha, eps, p, None, mass, None, o)))
+    _, stb = fg.fg_stats(h)
+    mass_err = float((mass - 1.0).abs().max())
+    k = 4
+    po = fg.fg_default_opts(mode=fg.FG_MODE_PLAIN)
+    t_plain = timed(lambda: fg.check(fg.fg_ppr_batch(h, s_d[:k], k, alpha, eps, p, None, None, None, po)))
+    deg = np.maximum(np.diff(g.row_ptr), 1).astype(np.float64)
+    sample = list(range(0, nq, nq // 16))[:16]
+    t0 = time.perf_counter()
+    pi = oracle.ppr_power(g, src[sample], alpha)
+    t_cpu = time.perf_counter() - t0
+    fg.check(fg.fg_ppr_batch(h, s_d, nq, alpha, eps, p, None, mass, None, o))
+    fg.check(fg.fg_sync())
+    ratio = max(float(np.max(np.abs(p[q].cpu().numpy().astype(np.float64) - pi[i]) / (eps * deg)))
+                for i, q in enumerate(sample))
+    res["rmat22_ppr"] = {"buffered_qps": nq / (t_buf / 1e3), "seeds": nq, "edge_pushes": int(stb.edges),
+                         "plain_gpu_qps": k / (t_plain / 1e3), "plain_sample": k,
+                         "cpu_oracle_qps": len(sample) / t_cpu, "cpu_sample": len(sample),
+                         "max_err_over_eps_deg": ratio, "mass_err_max": mass_err}
+    del p
+    fg.fg_graph_destroy(h)
+
+    # cfg 4: R-MAT s24 SSSP, batches of 256 of the 16,384 sources
+    name = "rmat24_sssp"
+    g, h = graph(name)
+    src = inputs.workload_sources(name, g)
+    nb = 256
+    s_d = torch.from_numpy(src[:nb]).to(dev)
+    out = torch.empty((nb, g.n), dtype=torch.int32, device=dev)
+    st, ob, rep = fg.fg_tune_opts(h, fg.FG_QUERY_SSSP, s_d[:64], 64)
+    fg.check(st)
+    t_buf = timed(lambda: fg.check(fg.fg_sssp_batch(h, s_d, nb, out, None, ob)))
+    _, stb = fg.fg_stats(h)
+    k = 4
+    t_plain = timed(lambda: fg.check(fg.fg_sssp_batch(h, s_d[:k], k, out, None,
+                                                      fg.fg_default_opts(mode=fg.FG_MODE_PLAIN))))
+    fg.check(fg.fg_sssp_batch(h, s_d, nb, out, None, ob))
+    fg.check(fg.fg_sync())
+    t0 = time.perf_counter()
+    ref = oracle.sssp(g, src[:16])
+    t_cpu = time.perf_counter() - t0
+    got = out[:16].cpu().numpy().view(np.uint32)
+    arcs = np.mean([oracle.reachable_arcs(g, r) for r in ref])
+    qps = nb / (t_buf / 1e3)
+    res["rmat24_sssp"] = {"buffered_qps": qps, "batch": nb, "gteps": qps * arcs / 1e9,
+                          "arcs_scanned_over_dijkstra": float(stb.edges) / (arcs * nb),
+                          "opts": {k2: int(getattr(ob, k2)) for k2 in ("sched", "sched_window", "delta")},
+                          "plain_gpu_qps": k / (t_plain / 1e3), "plain_sample": k,
+                          "cpu_oracle_qps": 16 / t_cpu, "cpu_sample": 16,
+                          "exact_sampled": bool(np.array_equal(got, ref)),
+                          "hbm_output_gbs": qps * 4 * g.n / 1e9}
+    fg.fg_graph_destroy(h)
+    print(json.dumps(res), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -388,6 +509,9 @@ def main():
         return
     if args.ablation:
         run_ablation(args)
+        return
+    if args.configs:
+        run_configs(args)
         return
     import torch
     ws, rank, local = dist_env()
