@@ -210,7 +210,9 @@ enum { FG_QUERY_SSSP = 0, FG_QUERY_BFS = 1, FG_QUERY_PPR = 2 };
  * typical). The tuner allocates nq * n * 4 B of output rows for the duration
  * of the call and runs each candidate once on `stream` (it synchronises).
  * report (nullable) receives the number of candidates and the default's and
- * the chosen schedule's batch times.
+ * the chosen schedule's batch times. The choice is cached in the graph per
+ * (kind, batch size rounded up to a power of two): a later call with the same
+ * key returns it without timing anything (report->candidates = 0).
  */
 typedef struct {
     int32_t candidates;

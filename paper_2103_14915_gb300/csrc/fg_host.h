@@ -5,7 +5,9 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "fg_internal.h"
 
@@ -78,6 +80,8 @@ struct fg_graph {
   int engine_qtype = -1;
   uint32_t max_degree = 0;
   double mean_weight = 1.0;        // mean arc weight (1 when unweighted)
+  // schedules chosen by fg_tune_opts, keyed by (query kind, log2 of the batch size rounded up)
+  std::map<std::pair<int, int>, std::pair<fg_opts, fg_tune_report>> tuned;
   int plain_blocks = 0, plain_threads = 0;
 };
 

@@ -42,6 +42,21 @@ extern "C" fg_status fg_tune_opts(fg_graph *g, int32_t kind, const int32_t *src,
   if (!g || !src || !best) return fail(FG_ERR_INVALID_ARG, "NULL argument");
   if (nq <= 0) return fail(FG_ERR_INVALID_ARG, "nq must be > 0");
   if (kind < FG_QUERY_SSSP || kind > FG_QUERY_PPR) return fail(FG_ERR_INVALID_ARG, "unknown query kind %d", kind);
+  int bucket = 0;
+  while ((1 << bucket) < nq && bucket < 30) ++bucket;
+  const std::pair<int, int> key(kind, bucket);
+  {
+    std::lock_guard<std::mutex> lk(g->mu);
+    auto it = g->tuned.find(key);
+    if (it != g->tuned.end()) {
+      *best = it->second.first;
+      if (report) {
+        *report = it->second.second;
+        report->candidates = 0;  // served from the cache
+      }
+      return FG_OK;
+    }
+  }
   CUDA_TRY(cudaSetDevice(g->device));
   DevBuf out;
   CUDA_TRY(out.reserve(4 * (size_t)nq * (size_t)g->n));
@@ -129,10 +144,14 @@ extern "C" fg_status fg_tune_opts(fg_graph *g, int32_t kind, const int32_t *src,
     }
   }
   *best = pick;
-  if (report) {
-    report->candidates = tried;
-    report->best_ms = pick_ms;
-    report->default_ms = base_ms;
+  fg_tune_report r;
+  r.candidates = tried;
+  r.best_ms = pick_ms;
+  r.default_ms = base_ms;
+  if (report) *report = r;
+  {
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->tuned[key] = std::make_pair(pick, r);
   }
   return FG_OK;
 }

@@ -37,6 +37,9 @@ def test_tuned_schedule_is_exact_and_not_slower(make, method, S, kind):
         fg.check(st)
         assert rep.candidates >= 2 and rep.best_ms <= rep.default_ms
         assert best.struct_size == fg.fg_default_opts().struct_size
+        st, again, rep2 = fg.fg_tune_opts(h, kind, s_d, len(srcs) - 1)  # same power-of-two bucket
+        fg.check(st)
+        assert rep2.candidates == 0 and bytes(again) == bytes(best)
         out = torch.empty((len(srcs), g.n), dtype=torch.int32, device=DEV)
         f = fg.fg_sssp_batch if kind == fg.FG_QUERY_SSSP else fg.fg_bfs_batch
         fg.check(f(h, s_d, len(srcs), out, None, best))
