@@ -118,17 +118,3 @@ __device__ __forceinline__ uint32_t sat_add_u32(uint32_t a, uint32_t b) {
 }
 
 }  // namespace fg
-
-namespace fg {
-
-// ---- 16-byte asynchronous global -> shared copies (cp.async, L2 only) ----
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
-  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-}
-
-}  // namespace fg

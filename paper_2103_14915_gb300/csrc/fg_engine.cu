@@ -35,6 +35,7 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kMaxVisitSteps = 1u << 22;  // relax/push steps of one visit before the watchdog fires
 constexpr uint32_t kBlockChunk = 16;            // work items a block claims at once
+constexpr uint32_t kTailChunk = 2;              // ... once fewer than 4 full chunks per block are left
 constexpr uint32_t kArenaChunk = 64;            // arena slots a warp reserves at once (>= 32)
 constexpr int kLaneMaxDeg = 8;                  // lane-per-vertex expansion for max out-degree <= 8
 
@@ -823,13 +824,18 @@ __device__ uint32_t claim_item(Ctrl *c, unsigned long long *claim, volatile int 
     const uint32_t pos = (uint32_t)old, end = (uint32_t)(old >> 32);
     if (pos < end) return pos;
     if (pos == end) {
-      uint32_t b = atomicAdd(&c->item_next, kBlockChunk);
+      // full chunks while plenty of work is left; near the end of the round
+      // small ones, so that no block takes several visits per warp into the tail
+      const uint32_t seen = *reinterpret_cast<volatile uint32_t *>(&c->item_next);
+      const uint32_t left = seen < tot ? tot - seen : 0u;
+      const uint32_t chunk = left > 4u * kBlockChunk * gridDim.x ? kBlockChunk : kTailChunk;
+      uint32_t b = atomicAdd(&c->item_next, chunk);
       if (ld_volatile_i32(&c->abort)) b = tot;
       if (b >= tot) {
         *done = 1;
         return kInvalidKey;
       }
-      const uint32_t e = min(tot, b + kBlockChunk);
+      const uint32_t e = min(tot, b + chunk);
       atomicExch(claim, ((unsigned long long)e << 32) | (unsigned long long)(b + 1u));
       return b;
     }
@@ -853,7 +859,8 @@ template <int QT>
 __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
   extern __shared__ __align__(16) uint32_t smem_dyn[];
   __shared__ unsigned long long s_scan[kWarps + 1];
-  __shared__ unsigned long long s_pre[2];
+  __shared__ unsigned long long s_pre[4];
+  __shared__ unsigned long long s_hv[kWarps];
   __shared__ unsigned long long s_claim;  // block's chunk of work items (claim_item)
   __shared__ int s_claim_done;
   constexpr bool kPPR = (QT == Q_PPR);
@@ -939,21 +946,25 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
     uint32_t *qb_nxt = a.qbest + (size_t)((round + 1u) & 1u) * (size_t)a.nq;
     // ---- SCAN-A: per-block totals ----
     {
-      unsigned long long loc = 0;
+      unsigned long long loc = 0, hv = 0;
       for (uint64_t k = k0 + threadIdx.x; k < k1; k += kThreads) {
         const uint32_t n_ops = __ldcg(a.cnt + k);
-        const bool act = n_ops > 0u || __ldcg(a.dirty + k) != 0u;
+        const bool dk = __ldcg(a.dirty + k) != 0u;
+        const bool act = n_ops > 0u || dk;
         loc += ((unsigned long long)n_ops << 32) | (act ? 1ull : 0ull);
+        hv += dk ? 1ull : 0ull;
         if (!kPPR && act && a.sched == FG_SCHED_PRIORITY)
           atomicMin(&qb_cur[k % (uint64_t)a.nq], __ldcg(a.prio + k));
       }
       loc = warp_sum(loc);
-      if (lane == 0) s_scan[wid] = loc;
+      hv = warp_sum(hv);
+      if (lane == 0) { s_scan[wid] = loc; s_hv[wid] = hv; }
       block_sync();
       if (threadIdx.x == 0) {
-        unsigned long long t = 0;
-        for (int i = 0; i < kWarps; ++i) t += s_scan[i];
+        unsigned long long t = 0, th = 0;
+        for (int i = 0; i < kWarps; ++i) { t += s_scan[i]; th += s_hv[i]; }
         a.blocksum[blockIdx.x] = t;
+        a.blocksum[gridDim.x + blockIdx.x] = th;
       }
     }
     if (!grid_barrier(c, gen, a.watchdog_ns)) goto done;
@@ -961,14 +972,34 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
     // ---- SCAN-B: work items, bin offsets, buffer reset ----
     unsigned long long tot_ops, tot_items, emitted;
     {
-      unsigned long long pre = 0, all = 0;
+      unsigned long long pre = 0, all = 0, preh = 0, allh = 0;
       for (int i = threadIdx.x; i < (int)gridDim.x; i += kThreads) {
         const unsigned long long v = __ldcg(a.blocksum + i);
+        const unsigned long long vh = __ldcg(a.blocksum + gridDim.x + i);
         all += v;
-        if (i < (int)blockIdx.x) pre += v;
+        allh += vh;
+        if (i < (int)blockIdx.x) { pre += v; preh += vh; }
       }
       pre = warp_sum(pre);
       all = warp_sum(all);
+      preh = warp_sum(preh);
+      allh = warp_sum(allh);
+      if (lane == 0) { s_hv[wid] = preh; }
+      block_sync();
+      if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int i = 0; i < kWarps; ++i) t += s_hv[i];
+        s_pre[2] = t;
+      }
+      block_sync();
+      if (lane == 0) { s_hv[wid] = allh; }
+      block_sync();
+      if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int i = 0; i < kWarps; ++i) t += s_hv[i];
+        s_pre[3] = t;
+      }
+      block_sync();
       if (lane == 0) s_scan[wid] = pre;
       block_sync();
       if (threadIdx.x == 0) {
@@ -996,7 +1027,8 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
         if (threadIdx.x == 0) raise_status(c, FG_ERR_TIMEOUT, kSiteRounds);
         break;
       }
-      unsigned long long run = pre;
+      unsigned long long run_ops = pre >> 32, run_items = pre & 0xFFFFFFFFull, run_h = s_pre[2];
+      const unsigned long long H = s_pre[3];
       const uint32_t window = a.sched_window;
       for (uint64_t t0 = k0; t0 < k1; t0 += kThreads) {
         const uint64_t k = t0 + threadIdx.x;
@@ -1007,12 +1039,17 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
           dflag = __ldcg(a.dirty + k);
           act = n_ops > 0u || dflag != 0u;
         }
-        const unsigned long long x = ((unsigned long long)n_ops << 32) | (act ? 1ull : 0ull);
+        // items that carry pending vertices from an earlier round (the
+        // wavefront of their query) take about twice as long on average: they
+        // are handed out first, so that the round's tail is short visits
+        const bool heavy = act && dflag != 0u;
+        const unsigned long long x = ((unsigned long long)n_ops << 32) | (act ? 1ull : 0ull) | (heavy ? (1ull << 16) : 0ull);
         unsigned long long tile_tot;
-        const unsigned long long ex = block_excl_scan(x, s_scan, tile_tot) + run;
+        const unsigned long long ex = block_excl_scan(x, s_scan, tile_tot);
         if (act) {
-          const uint32_t item_idx = (uint32_t)(ex & 0xFFFFFFFFull);
-          const uint32_t off = (uint32_t)(ex >> 32);
+          const unsigned long long I = run_items + (ex & 0xFFFFull), J = run_h + ((ex >> 16) & 0xFFFFull);
+          const uint32_t item_idx = (uint32_t)(heavy ? J : H + I - J);
+          const uint32_t off = (uint32_t)(run_ops + (ex >> 32));
           uint32_t fl = dflag ? 1u : 0u;
           if (!kPPR) {
             pr = __ldcg(a.prio + k);
@@ -1028,7 +1065,9 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
           a.cnt[k] = 0u;
           a.dirty[k] = 0u;
         }
-        run += tile_tot;
+        run_ops += tile_tot >> 32;
+        run_items += tile_tot & 0xFFFFull;
+        run_h += (tile_tot >> 16) & 0xFFFFull;
       }
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         c->rounds += 1ull;

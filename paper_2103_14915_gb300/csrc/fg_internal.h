@@ -15,7 +15,8 @@ constexpr uint32_t kInf = 0xFFFFFFFFu;
 constexpr uint32_t kInvalidKey = 0xFFFFFFFFu;
 
 // where a device status was raised (reported by fg_sync)
-enum : unsigned { kSiteNone = 0, kSiteBarrier = 1, kSiteStage = 2, kSiteVisit = 3, kSiteRounds = 4,
+// (site 2 is unused: it named a shared-memory staging wait that no longer exists)
+enum : unsigned { kSiteNone = 0, kSiteBarrier = 1, kSiteUnused2 = 2, kSiteVisit = 3, kSiteRounds = 4,
                   kSiteSource = 5, kSiteArena = 6, kSiteDegree = 7, kSiteClaim = 8 };
 
 // Graph in partition-major ("internal") vertex order. Partition j holds the
@@ -67,7 +68,7 @@ struct EngineArgs {
   uint32_t *qbest = nullptr;      // [nq] best pending value per query (priority scheduling)
   uint4 *items = nullptr;         // [K] {key, offset, count, flags}
   uint32_t *iprio = nullptr;      // [K] best value of each work item (priority carry-over)
-  unsigned long long *blocksum = nullptr;  // [grid] (ops << 32 | items) per block
+  unsigned long long *blocksum = nullptr;  // [2 * grid]: (ops << 32 | items) per block, then items with pending vertices
   // operation arena (append order) and bins (key order)
   uint32_t *e_key = nullptr;
   uint2 *e_op = nullptr;

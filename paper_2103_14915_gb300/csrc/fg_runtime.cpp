@@ -377,7 +377,7 @@ fg_status ensure_engine_ws(fg_graph *g, Workspace &ws, int qtype, int64_t nb, ui
     ws.pend_clean = false;
   }
   CUDA_TRY(ws.qbest.reserve(8 * (size_t)nb));
-  CUDA_TRY(ws.blocksum.reserve(8 * (size_t)blocks));
+  CUDA_TRY(ws.blocksum.reserve(16 * (size_t)blocks));
   CUDA_TRY(ws.e_key.reserve(4 * e_cap));
   CUDA_TRY(ws.e_op.reserve(8 * e_cap));
   CUDA_TRY(ws.b_op.reserve(8 * e_cap));
@@ -723,7 +723,7 @@ extern "C" fg_status fg_sync(void *stream_v) {
     if (first == FG_OK && c.status != 0) {
       const char *names[] = {"ok", "invalid argument", "out of memory", "CUDA error", "watchdog timeout",
                              "operation buffer overflow", "distance overflow", "unsupported"};
-      const char *sites[] = {"", " (device-wide barrier wait)", " (partition staging wait)",
+      const char *sites[] = {"", " (device-wide barrier wait)", "",
                              " (visit step limit)", " (max_rounds)", " (source id out of range)",
                              " (operation arena)", " (vertex degree out of range)", " (work-item claim wait)"};
       const int k = c.status >= 0 && c.status <= 7 ? c.status : 3;
