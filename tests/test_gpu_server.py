@@ -188,3 +188,41 @@ def test_budget_lowers_batch_size(graph):
         fg.fg_server_destroy(srv)
     st, _ = fg.fg_server_create(h, fg.fg_default_server_opts(lanes=2, hbm_budget=1000))
     assert st == fg.FG_ERR_OOM
+
+
+def test_destroy_with_batches_in_flight(graph):
+    g, h = graph
+    st, srv = fg.fg_server_create(h, fg.fg_default_server_opts(lanes=2, max_batch=8))
+    fg.check(st)
+    for s in inputs.sources_uniform(g, 12, seed=34):
+        fg.check(fg.fg_server_submit(srv, fg.FG_QUERY_SSSP, int(s))[0])
+    st, _ = fg.fg_server_poll(srv)  # launches both lanes
+    fg.check(st)
+    assert fg.fg_server_destroy(srv) == fg.FG_OK  # waits for the lanes, then frees
+    # the graph and the library stay usable
+    s_d = torch.tensor([0], dtype=torch.int32, device=DEV)
+    out = torch.empty((1, g.n), dtype=torch.int32, device=DEV)
+    fg.check(fg.fg_bfs_batch(h, s_d, 1, out, None, None))
+    fg.check(fg.fg_sync())
+    assert np.array_equal(out.cpu().numpy().view(np.uint32)[0], oracle.bfs(g, [0])[0])
+
+
+def test_directed_graph_mix():
+    g = inputs.rmat(10, 8, seed=12, directed=True, weights=(1, 255))  # has dangling vertices
+    st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, fg.fg_default_graph_opts())
+    fg.check(st)
+    try:
+        srcs = inputs.sources_uniform(g, 9, seed=35)
+        reqs = [(k % 3, int(s)) for k, s in enumerate(srcs)]
+        results, infos, _ = _run_mix(h, g, reqs, lanes=2, max_batch=3, waves=3)
+        for i, (kind, s) in enumerate(reqs):
+            assert infos[i][0] == fg.FG_OK
+            if kind == fg.FG_QUERY_PPR:
+                assert abs(infos[i][1] - 1.0) <= 1e-5  # mass, with dangling vertices returning to the source
+                pi = oracle.ppr_power(g, [s], ALPHA)[0]
+                assert np.all(results[i].astype(np.float64) <= pi + 1e-6)  # p approaches pi from below
+            else:
+                ref = oracle.sssp(g, [s])[0] if kind == fg.FG_QUERY_SSSP else oracle.bfs(g, [s])[0]
+                assert np.array_equal(results[i], ref)
+    finally:
+        fg.fg_graph_destroy(h)

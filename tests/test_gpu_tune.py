@@ -49,3 +49,16 @@ def test_tuned_schedule_is_exact_and_not_slower(make, method, S, kind):
         assert np.array_equal(out.cpu().numpy().view(np.uint32)[rows], ref)
     finally:
         fg.fg_graph_destroy(h)
+
+
+def test_ppr_keeps_the_default_schedule():
+    g = inputs.rmat(10, 8, seed=4)
+    st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, fg.fg_default_graph_opts())
+    fg.check(st)
+    try:
+        s_d = torch.from_numpy(inputs.sources_uniform(g, 16, seed=5)).to(DEV)
+        st, best, rep = fg.fg_tune_opts(h, fg.FG_QUERY_PPR, s_d, 16)
+        fg.check(st)
+        assert rep.candidates == 1 and best.sched == fg.FG_SCHED_FIFO and best.sched_window == 0
+    finally:
+        fg.fg_graph_destroy(h)
