@@ -947,6 +947,7 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
     // ---- SCAN-A: per-block totals ----
     {
       unsigned long long loc = 0, hv = 0;
+#pragma unroll 4
       for (uint64_t k = k0 + threadIdx.x; k < k1; k += kThreads) {
         const uint32_t n_ops = __ldcg(a.cnt + k);
         const bool dk = __ldcg(a.dirty + k) != 0u;
@@ -954,7 +955,7 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
         loc += ((unsigned long long)n_ops << 32) | (act ? 1ull : 0ull);
         hv += dk ? 1ull : 0ull;
         if (!kPPR && act && a.sched == FG_SCHED_PRIORITY)
-          atomicMin(&qb_cur[k % (uint64_t)a.nq], __ldcg(a.prio + k));
+          atomicMin(&qb_cur[(uint32_t)k % (uint32_t)a.nq], __ldcg(a.prio + k));
       }
       loc = warp_sum(loc);
       hv = warp_sum(hv);
@@ -1030,18 +1031,36 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
       unsigned long long run_ops = pre >> 32, run_items = pre & 0xFFFFFFFFull, run_h = s_pre[2];
       const unsigned long long H = s_pre[3];
       const uint32_t window = a.sched_window;
+      // tiles of kThreads keys; the next tile's counters are loaded while the
+      // current one is scanned and written (the block scan synchronises)
+      const bool by_window = !kPPR && a.sched == FG_SCHED_PRIORITY;
+      uint32_t nx_ops = 0, nx_dirty = 0, nx_prio = kInf, nx_qb = kInf;
+      {
+        const uint64_t k = k0 + threadIdx.x;
+        if (k < k1) {
+          nx_ops = __ldcg(a.cnt + k);
+          nx_dirty = __ldcg(a.dirty + k);
+          if (!kPPR) nx_prio = __ldcg(a.prio + k);
+          if (by_window) nx_qb = __ldcg(qb_cur + (uint32_t)k % (uint32_t)a.nq);
+        }
+      }
       for (uint64_t t0 = k0; t0 < k1; t0 += kThreads) {
         const uint64_t k = t0 + threadIdx.x;
-        uint32_t n_ops = 0, dflag = 0, pr = kInf;
-        bool act = false;
-        if (k < k1) {
-          n_ops = __ldcg(a.cnt + k);
-          dflag = __ldcg(a.dirty + k);
-          act = n_ops > 0u || dflag != 0u;
+        const uint32_t n_ops = nx_ops, dflag = nx_dirty, pr = nx_prio, qb = nx_qb;
+        const bool act = k < k1 && (n_ops > 0u || dflag != 0u);
+        {
+          const uint64_t kn = k + kThreads;
+          nx_ops = 0u;
+          nx_dirty = 0u;
+          nx_prio = kInf;
+          nx_qb = kInf;
+          if (kn < k1) {
+            nx_ops = __ldcg(a.cnt + kn);
+            nx_dirty = __ldcg(a.dirty + kn);
+            if (!kPPR) nx_prio = __ldcg(a.prio + kn);
+            if (by_window) nx_qb = __ldcg(qb_cur + (uint32_t)kn % (uint32_t)a.nq);
+          }
         }
-        // items that carry pending vertices from an earlier round (the
-        // wavefront of their query) take about twice as long on average: they
-        // are handed out first, so that the round's tail is short visits
         const bool heavy = act && dflag != 0u;
         const unsigned long long x = ((unsigned long long)n_ops << 32) | (act ? 1ull : 0ull) | (heavy ? (1ull << 16) : 0ull);
         unsigned long long tile_tot;
@@ -1052,11 +1071,7 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
           const uint32_t off = (uint32_t)(run_ops + (ex >> 32));
           uint32_t fl = dflag ? 1u : 0u;
           if (!kPPR) {
-            pr = __ldcg(a.prio + k);
-            if (a.sched == FG_SCHED_PRIORITY) {
-              const uint32_t qb = __ldcg(qb_cur + k % (uint64_t)a.nq);
-              if (pr > sat_add_u32(qb, window)) fl |= 2u;
-            }
+            if (by_window && pr > sat_add_u32(qb, window)) fl |= 2u;
             a.prio[k] = kInf;
           }
           a.items[item_idx] = make_uint4((uint32_t)k, off, n_ops, fl);
