@@ -91,7 +91,12 @@ typedef struct {
                                bitmaps (lossless). 0 = automatic: 128 per (partition, query)
                                buffer, clamped to [2^22, 2^29] */
     int32_t host_io;        /* 1: src and outputs are HOST pointers; the call copies them and
-                               completes before returning (fg_sync still reports status) */
+                               completes before returning (fg_sync still reports status).
+                               2: the same, asynchronous: the results are in the host buffers
+                               once fg_sync(stream) returns; until then the buffers must stay
+                               valid and unread. Each graph stages two such batches in turn,
+                               so one batch's copy to the host overlaps the next batch's
+                               kernels when they run on different streams */
     int32_t query_batch;    /* queries per device launch; 0 = all (bounded by workspace) */
     int32_t threads_per_vertex; /* SSSP/BFS expansion: 1 = one lane per frontier vertex (graphs
                                with out-degree <= 8 only), 32 or 0 (default) = a warp shares

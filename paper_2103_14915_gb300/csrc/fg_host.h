@@ -44,16 +44,37 @@ struct DevBuf {
   T *as() const { return reinterpret_cast<T *>(p); }
 };
 
+// Device staging of one host-I/O batch (sources, outputs). A workspace keeps
+// two, used in turn, so that one batch's copy to the host can overlap the next
+// batch's kernels; `done` is recorded after a slot's copy to the host.
+struct IoSlot {
+  DevBuf src, out, out2;
+  cudaEvent_t done = nullptr;
+  bool used = false;
+  void release() {
+    src.release();
+    out.release();
+    out2.release();
+    if (done) cudaEventDestroy(done);
+    done = nullptr;
+    used = false;
+  }
+};
+
 struct Workspace {
   DevBuf cnt, prio, dirty, cur, pend, qbest, items, iprio, blocksum, e_key, e_op, b_op, ctrl;
-  DevBuf scratch_r, scratch_c, scratch_p, state, io_src, io_out, io_out2;
+  DevBuf scratch_r, scratch_c, scratch_p, state;
   DevBuf pl_dist, pl_rr, pl_pp, pl_cc, pl_stamp, pl_f0, pl_f1, pl_sizes;
+  IoSlot io[2];
+  int io_next = 0;
   bool pend_clean = true;
   void release_all() {
     DevBuf *all[] = {&cnt, &prio, &dirty, &cur, &pend, &qbest, &items, &iprio, &blocksum, &e_key, &e_op,
-                     &b_op, &ctrl, &scratch_r, &scratch_c, &scratch_p, &state, &io_src, &io_out, &io_out2, &pl_dist, &pl_rr,
+                     &b_op, &ctrl, &scratch_r, &scratch_c, &scratch_p, &state, &pl_dist, &pl_rr,
                      &pl_pp, &pl_cc, &pl_stamp, &pl_f0, &pl_f1, &pl_sizes};
     for (DevBuf *b : all) b->release();
+    io[0].release();
+    io[1].release();
   }
 };
 

@@ -439,6 +439,7 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
   if (o.mode != FG_MODE_BUFFERED && o.mode != FG_MODE_PLAIN) return fail(FG_ERR_INVALID_ARG, "unknown mode");
   if (o.sched != FG_SCHED_FIFO && o.sched != FG_SCHED_PRIORITY) return fail(FG_ERR_INVALID_ARG, "unknown sched");
   if (o.query_batch < 0) return fail(FG_ERR_INVALID_ARG, "query_batch must be >= 0");
+  if (o.host_io < 0 || o.host_io > 2) return fail(FG_ERR_INVALID_ARG, "host_io must be 0, 1 or 2");
   if (o.threads_per_vertex != 0 && o.threads_per_vertex != 1 && o.threads_per_vertex != 32)
     return fail(FG_ERR_INVALID_ARG, "threads_per_vertex must be 0, 1 or 32");
   if (qtype == Q_PPR) o.sched = FG_SCHED_FIFO;  // PPR buffers are scheduled first-in first-out
@@ -457,23 +458,34 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
   double *mass = mass_in;
   const bool host_io = o.host_io != 0;
   const size_t row_elems = (size_t)nq * (size_t)n;
+  IoSlot *io = nullptr;
   if (host_io) {
     for (int32_t i = 0; i < nq; ++i)
       if (src_in[i] < 0 || src_in[i] >= n)
         return fail(FG_ERR_INVALID_ARG, "src[%d] = %d out of range", i, src_in[i]);
-    if (shared_ws && g->has_last) CUDA_TRY(cudaEventSynchronize(g->last_done));
+    // staging slots are used in turn; before a slot is refilled on this
+    // stream, its previous copy to the host (on whatever stream) must be done
+    io = &ws.io[ws.io_next];
+    ws.io_next ^= 1;
+    if (!io->done) CUDA_TRY(cudaEventCreateWithFlags(&io->done, cudaEventDisableTiming));
     const size_t mass_off = ((4 * (size_t)nq + 15) / 16) * 16;
-    CUDA_TRY(ws.io_src.reserve(mass_off + 8 * (size_t)nq));
-    CUDA_TRY(ws.io_out.reserve(4 * row_elems));
-    if (qtype == Q_PPR && r_in) CUDA_TRY(ws.io_out2.reserve(4 * row_elems));
-    CUDA_TRY(cudaMemcpyAsync(ws.io_src.p, src_in, 4 * (size_t)nq, cudaMemcpyHostToDevice, stream));
-    src = ws.io_src.as<int32_t>();
-    mass = mass_in ? reinterpret_cast<double *>(ws.io_src.as<char>() + mass_off) : nullptr;
+    const bool grow = io->src.bytes < mass_off + 8 * (size_t)nq || io->out.bytes < 4 * row_elems ||
+                      (qtype == Q_PPR && r_in && io->out2.bytes < 4 * row_elems);
+    if (io->used) {
+      if (grow) CUDA_TRY(cudaEventSynchronize(io->done));  // reallocation frees the old buffers
+      else CUDA_TRY(cudaStreamWaitEvent(stream, io->done, 0));
+    }
+    CUDA_TRY(io->src.reserve(mass_off + 8 * (size_t)nq));
+    CUDA_TRY(io->out.reserve(4 * row_elems));
+    if (qtype == Q_PPR && r_in) CUDA_TRY(io->out2.reserve(4 * row_elems));
+    CUDA_TRY(cudaMemcpyAsync(io->src.p, src_in, 4 * (size_t)nq, cudaMemcpyHostToDevice, stream));
+    src = io->src.as<int32_t>();
+    mass = mass_in ? reinterpret_cast<double *>(io->src.as<char>() + mass_off) : nullptr;
     if (qtype == Q_PPR) {
-      pout = ws.io_out.as<float>();
-      rout = r_in ? ws.io_out2.as<float>() : nullptr;
+      pout = io->out.as<float>();
+      rout = r_in ? io->out2.as<float>() : nullptr;
     } else {
-      dist = ws.io_out.as<uint32_t>();
+      dist = io->out.as<uint32_t>();
     }
   }
   if (shared_ws && g->has_last) CUDA_TRY(cudaStreamWaitEvent(stream, g->last_done, 0));
@@ -653,7 +665,9 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
     } else {
       CUDA_TRY(cudaMemcpyAsync(dist_in, dist, 4 * row_elems, cudaMemcpyDeviceToHost, stream));
     }
-    CUDA_TRY(cudaStreamSynchronize(stream));
+    CUDA_TRY(cudaEventRecord(io->done, stream));
+    io->used = true;
+    if (o.host_io == 1) CUDA_TRY(cudaStreamSynchronize(stream));
   }
   return FG_OK;
 }

@@ -259,6 +259,30 @@ def test_host_io_path():
         dg.close()
 
 
+def test_async_host_io_two_streams():
+    # host_io = 2: results land in host buffers at fg_sync; batches alternate between two
+    # staging slots, so several batches in flight on two streams must not disturb each other
+    g = inputs.grid(40, 40, 500, 100, seed=3, weights=(100, 10000))
+    dg = DevGraph(g, fg.FG_PART_GROW, 64)
+    try:
+        sets = [inputs.sources_uniform(g, 7, 10 + i) for i in range(5)]
+        outs = [np.full((7, g.n), 7, dtype=np.uint32) for _ in sets]
+        sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+        o = fg.fg_default_opts(host_io=2, watchdog_ms=10000)
+        for i, (srcs, out) in enumerate(zip(sets, outs)):
+            f = fg.fg_bfs_batch if i % 2 == 0 else fg.fg_sssp_batch
+            fg.check(f(dg.h, srcs, 7, out, sa if i % 2 == 0 else sb, o))
+        fg.check(fg.fg_sync(sa))
+        fg.check(fg.fg_sync(sb))
+        for i, (srcs, out) in enumerate(zip(sets, outs)):
+            ref = oracle.bfs(g, srcs) if i % 2 == 0 else oracle.sssp(g, srcs)
+            assert np.array_equal(out, ref), i
+        assert fg.fg_sssp_batch(dg.h, sets[0], 7, outs[0], None, fg.fg_default_opts(host_io=3)) == \
+            fg.FG_ERR_INVALID_ARG
+    finally:
+        dg.close()
+
+
 def test_query_batch_split():
     g = inputs.rmat(10, 8, seed=9, weights=(1, 255))
     dg = DevGraph(g, fg.FG_PART_RANGE, 64)
