@@ -109,3 +109,65 @@ def test_rmat24_sssp_full_graph_batch():
         assert oracle.certificate_batch(g, srcs[sample], cert, weighted=True) == 0
     finally:
         fg.fg_graph_destroy(h)
+
+
+def test_rmat25_serving_full_graph():
+    """Requests of every kind through the serving loop on the directed R-MAT scale-25 graph."""
+    import time
+
+    class _Row:
+        def __init__(self, ptr, n, typestr):
+            self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
+                                             "version": 3}
+
+    name = "rmat25_serving"
+    alpha, eps = 0.15, 1e-6
+    g = inputs.workload_graph(name)
+    h = _graph(g, fg.FG_PART_AUTO, 0)
+    srv = None
+    try:
+        srcs = inputs.workload_sources(name, g, k=6)
+        kinds = [fg.FG_QUERY_SSSP, fg.FG_QUERY_BFS, fg.FG_QUERY_PPR] * 2
+        so = fg.fg_default_server_opts(lanes=2, max_batch=4, alpha=alpha, eps=eps)
+        so.opts[fg.FG_QUERY_SSSP].sched, so.opts[fg.FG_QUERY_SSSP].sched_window = 1, 4
+        st, srv = fg.fg_server_create(h, so)
+        fg.check(st)
+        ids = {}
+        for k, s in zip(kinds, srcs):
+            st, rid = fg.fg_server_submit(srv, k, int(s))
+            fg.check(st)
+            ids[rid] = (k, int(s))
+        rows, t_end = {}, time.time() + 600
+        while len(rows) < len(ids):
+            assert time.time() < t_end
+            st, done = fg.fg_server_poll(srv)
+            fg.check(st)
+            for rid in done:
+                st, info = fg.fg_server_info(srv, rid)
+                fg.check(st)
+                assert info.status == fg.FG_OK
+                k, s = ids[rid]
+                typ = "<f4" if k == fg.FG_QUERY_PPR else "<i4"
+                row = torch.as_tensor(_Row(info.result, g.n, typ), device=DEV).clone().cpu().numpy()
+                res = torch.as_tensor(_Row(info.residual, g.n, "<f4"), device=DEV).clone().cpu().numpy() \
+                    if k == fg.FG_QUERY_PPR else None
+                rows[rid] = (k, s, row, res, info.mass)
+                fg.check(fg.fg_server_release(srv, rid))
+        checked = set()
+        deg = np.maximum(np.diff(g.row_ptr), 1).astype(np.float32)
+        for rid, (k, s, row, res, mass) in rows.items():
+            if k == fg.FG_QUERY_PPR:
+                assert abs(mass - 1.0) <= 1e-5
+                assert (res < eps * deg).all() and (row >= 0).all() and (res >= 0).all()
+                continue
+            d = row.view(np.uint32)
+            weighted = k == fg.FG_QUERY_SSSP
+            assert oracle.certificate_batch(g, [s], d[None, :], weighted=weighted) == 0
+            if k not in checked:  # one row per kind against the oracle itself
+                ref = oracle.sssp(g, [s])[0] if weighted else oracle.bfs(g, [s])[0]
+                assert np.array_equal(d, ref)
+                checked.add(k)
+    finally:
+        if srv is not None:
+            fg.fg_server_destroy(srv)
+        fg.fg_graph_destroy(h)
