@@ -577,7 +577,8 @@ __device__ __forceinline__ float ppr_thr(const uint32_t *prp, float eps, uint32_
 }
 
 
-__device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, const uint32_t *prp, Counters &ctr) {
+__device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, const uint32_t *prp, Counters &ctr,
+                          ArenaSlots &sl) {
   const DevGraph &g = a.g;
   const int lane = lane_id();
   const uint32_t key = item.x, off = item.y, cnt = item.z, flags = item.w;
@@ -669,9 +670,24 @@ __device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, c
         }
         n_ext += __popc(__ballot_sync(kFull, ext));
       }
+      // reserve the batch's cross-partition increments together, from the
+      // warp's own arena chunk (a new chunk of at least kArenaChunk slots
+      // when it runs short)
       unsigned long long rbase = 0;
-      if (lane == 0 && n_ext) rbase = atomicAdd(&a.ctrl->e_cursor, (unsigned long long)n_ext);
-      rbase = __shfl_sync(kFull, rbase, 0);
+      if (n_ext) {
+        if (sl.pos + n_ext > sl.end) {
+          release_slots(a, sl);
+          const unsigned long long want = n_ext > kArenaChunk ? (unsigned long long)n_ext : kArenaChunk;
+          unsigned long long b = 0;
+          if (lane == 0) b = atomicAdd(&a.ctrl->e_cursor, want);
+          b = __shfl_sync(kFull, b, 0);
+          sl.pos = b;
+          sl.end = b + want;
+          sl.seen = sl.end;
+        }
+        rbase = sl.pos;
+        sl.pos += n_ext;
+      }
       if (n_ext && rbase + n_ext > a.e_cap) {
         // does not fit this round: keep these vertices for a later visit
         if (n_ext > a.e_cap) raise_status(a.ctrl, FG_ERR_BIN_OVERFLOW, kSiteArena);
@@ -1154,7 +1170,7 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
         if (defer) {
           carry_item(a, it, __ldcg(a.iprio + idx));
         } else if (kPPR) {
-          visit_ppr(a, w, it, prp, ctr);
+          visit_ppr(a, w, it, prp, ctr, sl);
         } else {
           const uint32_t q = it.x - p * (uint32_t)a.nq;
           const uint32_t qbound =
