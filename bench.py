@@ -343,16 +343,16 @@ def run_ablation(args):
         return a.elapsed_time(b), d, out
 
     ref = {}
-    for S in (256, 512, 1024, 2048):
+    for S, method in ((256, fg.FG_PART_GROW), (512, fg.FG_PART_GROW), (1024, fg.FG_PART_GROW),
+                      (2048, fg.FG_PART_GROW), (1024, fg.FG_PART_RANGE)):
         st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0,
-                                      fg.fg_default_graph_opts(partition_method=fg.FG_PART_GROW,
-                                                               partition_vertices=S))
+                                      fg.fg_default_graph_opts(partition_method=method, partition_vertices=S))
         fg.check(st)
         info = fg.fg_graph_info(h)[1]
         mu = g.m // max(1, info.num_partitions) // nq  # arcs per partition per query (yield heuristic 1 unit)
         cfgs = [("fifo", {}, {}),
                 ("priority-window", TUNED_BFS, TUNED_SSSP)]
-        if S == 1024:
+        if S == 1024 and method == fg.FG_PART_GROW:
             cfgs += [("priority-window/2", {"sched": 1, "sched_window": TUNED_BFS["sched_window"] // 2},
                       {"sched": 1, "sched_window": TUNED_SSSP["sched_window"] // 2}),
                      ("priority-window*2", {"sched": 1, "sched_window": TUNED_BFS["sched_window"] * 2},
@@ -365,7 +365,8 @@ def run_ablation(args):
                      ("lane-per-vertex expansion", dict(TUNED_BFS, threads_per_vertex=1),
                       dict(TUNED_SSSP, threads_per_vertex=1))]
         for name, ob, os_ in cfgs:
-            row = {"S": S, "config": name, "cut_arcs": int(info.cut_arcs)}
+            row = {"S": S, "partition": "grow" if method == fg.FG_PART_GROW else "range", "config": name,
+                   "cut_arcs": int(info.cut_arcs)}
             for kind, o in (("bfs", ob), ("sssp", os_)):
                 ms, d, out = run(h, kind, o)
                 key = kind

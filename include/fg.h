@@ -55,7 +55,8 @@ typedef struct fg_graph fg_graph;
 enum {
     FG_PART_AUTO = 0,    /* GROW when the id order has little locality, else RANGE */
     FG_PART_RANGE = 1,   /* contiguous id ranges [i*S, (i+1)*S): the paper's equal-vertex split */
-    FG_PART_GROW = 2     /* breadth-first region growing to S vertices (stand-in for METIS) */
+    FG_PART_GROW = 2,    /* breadth-first region growing to S vertices (stand-in for METIS) */
+    FG_PART_DEGREE = 3   /* vertices by out-degree, highest first (hubs share partitions) */
 };
 
 typedef struct {
@@ -122,7 +123,7 @@ typedef struct {
     int64_t n, m;
     int32_t partition_vertices;  /* S */
     int32_t num_partitions;      /* |P| */
-    int32_t partition_method;    /* FG_PART_RANGE or FG_PART_GROW (after AUTO) */
+    int32_t partition_method;    /* FG_PART_RANGE, FG_PART_GROW or FG_PART_DEGREE (after AUTO) */
     int32_t weighted;
     int64_t cut_arcs;            /* arcs whose endpoints lie in different partitions */
     int64_t device_bytes;        /* graph bytes resident on the device */
@@ -194,7 +195,7 @@ fg_status fg_stats(const fg_graph *g, fg_stats_t *out);
 /*
  * Host-only partitioner, exposed for inspection: writes perm[i] = original id
  * of internal vertex i (partition j holds internal ids [j*S, (j+1)*S)).
- * Makes no CUDA call. method is FG_PART_RANGE or FG_PART_GROW.
+ * Makes no CUDA call. method is FG_PART_RANGE, FG_PART_GROW or FG_PART_DEGREE.
  */
 fg_status fg_partition_plan(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t method,
                             int32_t partition_vertices, int32_t *perm);

@@ -6,9 +6,13 @@
 // social graphs (Sec. 6.1). GROW grows each partition breadth-first from the
 // smallest unassigned id until it holds S vertices; on road-like graphs it
 // yields compact regions with few cut edges and stands in for the METIS
-// edge-cut partitioning the paper applies to road networks (Sec. 6.1). Within
-// a partition, vertices are ordered by original id so that a partition's state
-// maps to runs of consecutive ids in the caller's query-major arrays.
+// edge-cut partitioning the paper applies to road networks (Sec. 6.1). DEGREE
+// orders the vertices by out-degree, highest first, so the hubs of a
+// power-law graph share partitions and the arcs among them stay inside one
+// (a cheap ordering in the spirit of the locality-improving orderings the
+// paper's partition study discusses, Sec. 6.4). Within a GROW partition,
+// vertices are ordered by original id so that a partition's state maps to
+// runs of consecutive ids in the caller's query-major arrays.
 #include <algorithm>
 #include <cstdint>
 #include <vector>
@@ -23,6 +27,14 @@ bool partition_plan_impl(int64_t n, const int64_t *row_ptr, const int32_t *col, 
   if (n < 1 || S < 1 || !perm) return false;
   if (method == FG_PART_RANGE) {
     for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
+    return true;
+  }
+  if (method == FG_PART_DEGREE) {
+    if (!row_ptr) return false;
+    for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
+    std::stable_sort(perm, perm + n, [&](int32_t a, int32_t b) {
+      return row_ptr[a + 1] - row_ptr[a] > row_ptr[b + 1] - row_ptr[b];
+    });
     return true;
   }
   if (method != FG_PART_GROW || !row_ptr || !col) return false;

@@ -107,10 +107,10 @@ extern "C" fg_status fg_partition_plan(int64_t n, const int64_t *row_ptr, const 
                                        int32_t partition_vertices, int32_t *perm) {
   if (n < 1 || n >= (int64_t(1) << 31) || !perm || partition_vertices < 1)
     return fail(FG_ERR_INVALID_ARG, "fg_partition_plan: bad arguments");
-  if (method != FG_PART_RANGE && method != FG_PART_GROW)
-    return fail(FG_ERR_INVALID_ARG, "fg_partition_plan: method must be FG_PART_RANGE or FG_PART_GROW");
-  if (method == FG_PART_GROW && (!row_ptr || !col))
-    return fail(FG_ERR_INVALID_ARG, "fg_partition_plan: GROW needs the CSR");
+  if (method != FG_PART_RANGE && method != FG_PART_GROW && method != FG_PART_DEGREE)
+    return fail(FG_ERR_INVALID_ARG, "fg_partition_plan: method must be FG_PART_RANGE, FG_PART_GROW or FG_PART_DEGREE");
+  if ((method == FG_PART_GROW && !col) || (method != FG_PART_RANGE && !row_ptr))
+    return fail(FG_ERR_INVALID_ARG, "fg_partition_plan: GROW and DEGREE need the CSR");
   if (!partition_plan_impl(n, row_ptr, col, method, partition_vertices, perm))
     return fail(FG_ERR_INVALID_ARG, "fg_partition_plan failed");
   return FG_OK;
@@ -151,7 +151,7 @@ extern "C" fg_status fg_graph_create_ex(int64_t n, int64_t m, const int64_t *row
     go.partition_method = gopts_in->partition_method;
     go.partition_vertices = gopts_in->partition_vertices;
   }
-  if (go.partition_method < FG_PART_AUTO || go.partition_method > FG_PART_GROW)
+  if (go.partition_method < FG_PART_AUTO || go.partition_method > FG_PART_DEGREE)
     return fail(FG_ERR_INVALID_ARG, "unknown partition method %d", go.partition_method);
   if (go.partition_vertices != 0 &&
       (go.partition_vertices < 32 || go.partition_vertices > 4096 ||

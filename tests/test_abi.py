@@ -136,6 +136,21 @@ def test_partition_plan_is_a_permutation_with_compact_regions(lib, S):
     assert grow_cut < 0.6 * range_cut, (grow_cut, range_cut)
 
 
+def test_degree_plan_orders_by_degree_and_keeps_hub_arcs_inside(lib):
+    g = inputs.rmat(12, 16, seed=3)
+    S = 256
+    perm = np.empty(g.n, dtype=np.int32)
+    assert fg.fg_partition_plan(g.n, g.row_ptr, g.col, fg.FG_PART_DEGREE, S, perm) == fg.FG_OK
+    assert np.array_equal(np.sort(perm), np.arange(g.n))
+    deg = np.diff(g.row_ptr)[perm]
+    assert np.all(np.diff(deg) <= 0)  # out-degree non-increasing along the internal order
+    ties = np.flatnonzero(np.diff(deg) == 0)
+    assert np.all(perm[ties] < perm[ties + 1])  # stable: equal degrees keep id order
+    rng = np.arange(g.n, dtype=np.int32)
+    assert _cut(g, perm, S) < _cut(g, rng, S)  # hubs sharing partitions keep some arcs inside
+    assert fg.fg_partition_plan(g.n, None, None, fg.FG_PART_DEGREE, S, perm) == fg.FG_ERR_INVALID_ARG
+
+
 def test_partition_plan_bad_args(lib):
     perm = np.empty(4, dtype=np.int32)
     assert fg.fg_partition_plan(4, None, None, fg.FG_PART_GROW, 2, perm) == fg.FG_ERR_INVALID_ARG

@@ -91,7 +91,8 @@ GRAPHS = small_graphs()
 
 
 @pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=[g.name for g in GRAPHS])
-@pytest.mark.parametrize("method,S", [(fg.FG_PART_RANGE, 32), (fg.FG_PART_GROW, 64), (fg.FG_PART_AUTO, 0)])
+@pytest.mark.parametrize("method,S", [(fg.FG_PART_RANGE, 32), (fg.FG_PART_GROW, 64), (fg.FG_PART_AUTO, 0),
+                                      (fg.FG_PART_DEGREE, 32)])
 def test_sssp_bfs_exact_small(gi, method, S):
     g = GRAPHS[gi]
     dg = DevGraph(g, method, S)
@@ -182,7 +183,7 @@ def check_ppr(g, srcs, p, r, mass, alpha, eps, directed=False):
 
 
 @pytest.mark.parametrize("gi", [0, 1, 3, 4, 5, 6, 7, 8], ids=[GRAPHS[i].name for i in [0, 1, 3, 4, 5, 6, 7, 8]])
-@pytest.mark.parametrize("method,S", [(fg.FG_PART_RANGE, 32), (fg.FG_PART_GROW, 64)])
+@pytest.mark.parametrize("method,S", [(fg.FG_PART_RANGE, 32), (fg.FG_PART_GROW, 64), (fg.FG_PART_DEGREE, 32)])
 def test_ppr_bound_small(gi, method, S):
     g = GRAPHS[gi]
     dg = DevGraph(g, method, S)
