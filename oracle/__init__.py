@@ -59,6 +59,7 @@ def _load():
         lib.orc_sssp_certificate.argtypes = [i64, p, p, p, i32, p]
         lib.orc_bfs_certificate.argtypes = [i64, p, p, i32, p]
         lib.orc_certificate_batch.argtypes = [i64, p, p, p, i32, p, p]
+        lib.orc_ncp_sweep_batch.argtypes = [i64, p, p, i32, p, i32, p, p, p]
         lib.orc_certificate_batch.restype = i64
         _lib = lib
     return _lib
@@ -164,3 +165,19 @@ def reachable_arcs(g, dist_row: np.ndarray) -> int:
     """Arcs whose tail is reachable (the edges a sequential Dijkstra/BFS scans)."""
     deg = np.diff(g.row_ptr)
     return int(deg[dist_row != UNREACHED].sum())
+
+
+def ncp_sweep(g, p_rows: np.ndarray, top: int):
+    """Sweep cuts over PPR vectors (rows of p_rows). Returns (order int32[nq, top],
+    phi float64[nq, top], count int32[nq]); entries past count are unused."""
+    lib = _load()
+    rp, col, _ = _csr(g)
+    pr = np.ascontiguousarray(np.atleast_2d(p_rows), dtype=np.float32)
+    nq = pr.shape[0]
+    order = np.full((nq, top), -1, dtype=np.int32)
+    phi = np.full((nq, top), np.nan, dtype=np.float64)
+    count = np.zeros(nq, dtype=np.int32)
+    r = lib.orc_ncp_sweep_batch(g.n, _p(rp), _p(col), nq, _p(pr), int(top), _p(order), _p(phi), _p(count))
+    if r != 0:
+        raise RuntimeError(f"orc_ncp_sweep_batch failed ({r})")
+    return order, phi, count

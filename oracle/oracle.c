@@ -24,6 +24,13 @@
  *                 (1-alpha) r(v) to the source); r(v) = 0. A diagnostic second
  *                 answer, not the parity target.
  *   orc_*_certificate  implementation-free checks of a distance / level array.
+ *   orc_ncp_sweep sweep cut over one PPR vector, the step of the network
+ *                 community profile (NCP) application that runs many PPRs
+ *                 (Sec. 1, 6.1): vertices with p(v) > 0 ordered by
+ *                 p(v) / max(d(v), 1) (computed in FP32), largest first, ties
+ *                 by smaller id; for each prefix S_k of the first `top` of them
+ *                 the conductance cut(S_k) / min(vol(S_k), vol(V) - vol(S_k)),
+ *                 vol = sum of degrees, cut = arcs leaving S_k (undirected).
  *
  * Unreachable vertices hold UINT32_MAX. Batches run one query per OpenMP
  * thread, the paper's best CPU scheme ("t = 1", Sec. 1 and 6.1).
@@ -353,6 +360,73 @@ static int certificate(int64_t n, const int64_t *row_ptr, const int32_t *col, co
     }
     free(has_parent); free(seen); free(q);
     return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* sweep cut (NCP)                                                           */
+/* ------------------------------------------------------------------------ */
+typedef struct { float key; int32_t v; } swent;
+
+static int sweep_cmp(const void *a, const void *b) {
+    const swent *x = (const swent *)a, *y = (const swent *)b;
+    if (x->key > y->key) return -1;
+    if (x->key < y->key) return 1;
+    return (x->v > y->v) - (x->v < y->v);
+}
+
+/* order[k] = k-th vertex of the sweep, phi[k] = conductance of the first k + 1
+   vertices (1.0 when the smaller volume is 0). Returns the number of prefixes
+   (<= top), or a negative error. */
+int orc_ncp_sweep(int64_t n, const int64_t *row_ptr, const int32_t *col, const float *p, int32_t top,
+                  int32_t *order, double *phi) {
+    if (n < 1 || top < 1) return -1;
+    swent *c = (swent *)malloc((size_t)n * sizeof(swent));
+    int32_t *rank = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (!c || !rank) { free(c); free(rank); return -2; }
+    int64_t nc = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        rank[v] = -1;
+        if (p[v] > 0.0f) {
+            const int64_t d = row_ptr[v + 1] - row_ptr[v];
+            c[nc].key = p[v] / (float)(d > 0 ? d : 1);
+            c[nc].v = (int32_t)v;
+            ++nc;
+        }
+    }
+    qsort(c, (size_t)nc, sizeof(swent), sweep_cmp);
+    const int64_t k_max = nc < top ? nc : top;
+    for (int64_t k = 0; k < k_max; ++k) { order[k] = c[k].v; rank[c[k].v] = (int32_t)k; }
+    const int64_t vol_all = row_ptr[n];
+    int64_t cut = 0, vol = 0;
+    for (int64_t k = 0; k < k_max; ++k) {
+        const int32_t v = order[k];
+        int64_t inside = 0;  /* neighbours already in the set */
+        for (int64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+            const int32_t r = rank[col[e]];
+            if (r >= 0 && r < k) ++inside;
+        }
+        const int64_t d = row_ptr[v + 1] - row_ptr[v];
+        cut += d - (g_mutation == 6 ? inside : 2 * inside);  /* planted 6: internal arcs counted once */
+        vol += d;
+        const int64_t den = vol < vol_all - vol ? vol : vol_all - vol;
+        phi[k] = den > 0 ? (double)cut / (double)den : 1.0;
+    }
+    free(c);
+    free(rank);
+    return (int)k_max;
+}
+
+int orc_ncp_sweep_batch(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t nq, const float *p,
+                        int32_t top, int32_t *order, double *phi, int32_t *count) {
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (int32_t q = 0; q < nq; ++q) {
+        const int r = orc_ncp_sweep(n, row_ptr, col, p + (size_t)q * (size_t)n, top, order + (size_t)q * top,
+                                    phi + (size_t)q * top);
+        count[q] = r;
+        if (r < 0) bad |= 1;
+    }
+    return bad ? -1 : 0;
 }
 
 int orc_sssp_certificate(int64_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *w,
