@@ -33,7 +33,7 @@ def build(force: bool = False) -> Path:
     """Compile oracle.c (gcc -O2, OpenMP over queries) into an in-tree .so."""
     if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
         tmp = _LIB.with_suffix(f".{os.getpid()}.tmp")
-        subprocess.run(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", str(_SRC), "-lm",
+        subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC", "-std=c11", str(_SRC), "-lm",
                         "-o", str(tmp)], check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -60,6 +60,8 @@ def _load():
         lib.orc_bfs_certificate.argtypes = [i64, p, p, i32, p]
         lib.orc_certificate_batch.argtypes = [i64, p, p, p, i32, p, p]
         lib.orc_ncp_sweep_batch.argtypes = [i64, p, p, i32, p, i32, p, p, p]
+        lib.orc_ll_query.argtypes = [i64, i32, p, i64, p, p]
+        lib.orc_bc_batch.argtypes = [i64, p, p, p, ctypes.c_int, i32, p, p, p]
         lib.orc_certificate_batch.restype = i64
         _lib = lib
     return _lib
@@ -85,7 +87,9 @@ def num_threads() -> int:
 
 def set_mutation(k: int) -> None:
     """Plant a known mistake (tests only): 1 ignore weights, 2 skip last arc,
-    3 BFS levels start at 1, 4 PPR transposed operand, 5 PPR drops dangling mass."""
+    3 BFS levels start at 1, 4 PPR transposed operand, 5 PPR drops dangling mass,
+    6 sweep counts internal arcs once, 7 LL query ignores unreachable landmarks' sentinel,
+    8 BC dependency drops the 1 of (1 + delta(w))."""
     _load().orc_set_mutation(int(k))
 
 
@@ -181,3 +185,39 @@ def ncp_sweep(g, p_rows: np.ndarray, top: int):
     if r != 0:
         raise RuntimeError(f"orc_ncp_sweep_batch failed ({r})")
     return order, phi, count
+
+
+def ll_labels(dist_rows: np.ndarray) -> np.ndarray:
+    """Label construction of landmark labeling: the batch's distance rows
+    (query-major uint32[K, n], row k = d(s_k, .)) as per-vertex labels
+    (vertex-major uint32[n, K]): labels[v, k] = d(s_k, v)."""
+    return np.ascontiguousarray(np.asarray(dist_rows, dtype=np.uint32).T)
+
+
+def ll_query(labels: np.ndarray, pairs: np.ndarray) -> np.ndarray:
+    """Landmark distance estimates for pairs (int32[Q, 2]): min over landmarks
+    reaching both of d(s, u) + d(s, v) (uint64), UINT64_MAX when none does."""
+    lib = _load()
+    lab = np.ascontiguousarray(labels, dtype=np.uint32)
+    pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    out = np.empty(pr.shape[0], dtype=np.uint64)
+    r = lib.orc_ll_query(lab.shape[0], lab.shape[1], _p(lab), pr.shape[0], _p(pr), _p(out))
+    if r != 0:
+        raise ValueError("vertex id out of range")
+    return out
+
+
+def bc(g, srcs, weighted: bool):
+    """Betweenness centrality from the sources srcs (Brandes' dependencies summed
+    over the sources in order): returns (bc float64[n], sigma_max, exact), exact
+    False when some shortest-path count reached 2^53."""
+    lib = _load()
+    rp, col, w = _csr(g)
+    srcs = np.ascontiguousarray(np.atleast_1d(srcs), dtype=np.int32)
+    out = np.empty(g.n, dtype=np.float64)
+    smax = np.zeros(1, dtype=np.float64)
+    r = lib.orc_bc_batch(g.n, _p(rp), _p(col), _p(w) if weighted else None, 1 if weighted else 0, srcs.size,
+                         _p(srcs), _p(out), _p(smax))
+    if r < 0:
+        raise ValueError(f"orc_bc_batch failed ({r})")
+    return out, float(smax[0]), r == 0

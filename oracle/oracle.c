@@ -31,6 +31,21 @@
  *                 by smaller id; for each prefix S_k of the first `top` of them
  *                 the conductance cut(S_k) / min(vol(S_k), vol(V) - vol(S_k)),
  *                 vol = sum of degrees, cut = arcs leaving S_k (undirected).
+ *   orc_bc_batch  betweenness centrality from sampled sources (BC, Sec. 1, 6.1:
+ *                 one SSSP per source on a weighted graph, one BFS on an
+ *                 unweighted one, then the dependency accumulation of Brandes,
+ *                 the algorithm the paper cites): the oracle's own Dijkstra /
+ *                 BFS, sigma = number of shortest paths (pushed along tight
+ *                 arcs in nondecreasing distance order), the dependency
+ *                 delta(v) = sum over tight out-arcs (v, w), in CSR order, of
+ *                 sigma(v) / sigma(w) * (1 + delta(w)), and
+ *                 bc(v) = sum over sources s != v, in batch order, of delta_s(v).
+ *                 Each operation is one IEEE double operation in that order
+ *                 (built with -ffp-contract=off: no fused multiply-add).
+ *   orc_ll_query  landmark labeling (LL, Sec. 1, 6.1: labels from a batch of
+ *                 SSSPs from landmark vertices): with labels[v][k] = d(s_k, v),
+ *                 the distance estimate of a pair (u, v) is the minimum over
+ *                 landmarks reaching both of d(s_k, u) + d(s_k, v).
  *
  * Unreachable vertices hold UINT32_MAX. Batches run one query per OpenMP
  * thread, the paper's best CPU scheme ("t = 1", Sec. 1 and 6.1).
@@ -425,6 +440,128 @@ int orc_ncp_sweep_batch(int64_t n, const int64_t *row_ptr, const int32_t *col, i
                                     phi + (size_t)q * top);
         count[q] = r;
         if (r < 0) bad |= 1;
+    }
+    return bad ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* betweenness centrality (BC)                                               */
+/* ------------------------------------------------------------------------ */
+typedef struct { uint32_t d; int32_t v; } dvent;
+
+static int dv_cmp(const void *a, const void *b) {
+    const dvent *x = (const dvent *)a, *y = (const dvent *)b;
+    if (x->d != y->d) return x->d < y->d ? -1 : 1;
+    return (x->v > y->v) - (x->v < y->v);
+}
+
+/* One source: dist (from orc_sssp / orc_bfs), sigma and delta (double[n]).
+   Returns 0, 1 if some sigma reached 2^53 (then sums of path counts may have
+   rounded), or a negative error. Arcs of weight 0 are rejected (-4): they
+   would put equal-distance vertices on shortest paths of each other. */
+static int bc_one(int64_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *w, int32_t src,
+                  const uint32_t *dist, double *sigma, double *delta, dvent *ord) {
+    int64_t nr = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        sigma[v] = 0.0;
+        delta[v] = 0.0;
+        if (dist[v] != UINT32_MAX) { ord[nr].d = dist[v]; ord[nr].v = (int32_t)v; ++nr; }
+    }
+    qsort(ord, (size_t)nr, sizeof(dvent), dv_cmp);
+    sigma[src] = 1.0;
+    int inexact = 0;
+    for (int64_t i = 0; i < nr; ++i) {                 /* sigma, nondecreasing distance */
+        const int32_t u = ord[i].v;
+        for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+            const int32_t x = col[e];
+            const uint64_t wt = w ? (uint64_t)w[e] : 1u;
+            if (w && w[e] == 0) return -4;
+            if (dist[x] != UINT32_MAX && (uint64_t)dist[u] + wt == (uint64_t)dist[x]) {
+                sigma[x] = sigma[x] + sigma[u];
+                if (sigma[x] >= 9007199254740992.0) inexact = 1;
+            }
+        }
+    }
+    for (int64_t i = nr - 1; i >= 0; --i) {            /* delta, nonincreasing distance */
+        const int32_t u = ord[i].v;
+        double acc = 0.0;
+        for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+            const int32_t x = col[e];
+            const uint64_t wt = w ? (uint64_t)w[e] : 1u;
+            if (dist[x] != UINT32_MAX && (uint64_t)dist[u] + wt == (uint64_t)dist[x]) {
+                const double ratio = sigma[u] / sigma[x];
+                const double term = g_mutation == 8 ? delta[x] : 1.0 + delta[x];  /* planted 8: drops the 1 */
+                acc = acc + ratio * term;
+            }
+        }
+        delta[u] = acc;
+    }
+    return inexact;
+}
+
+/* bc[v] (double[n]) = sum over q in order of delta_{srcs[q]}(v), v != srcs[q];
+   weighted != 0: SSSP distances over w, else BFS levels. sigma_max (nullable)
+   receives the largest path count. Returns 0, 1 (some path count reached 2^53)
+   or a negative error. */
+int orc_bc_batch(int64_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *w, int weighted, int32_t nq,
+                 const int32_t *srcs, double *bc, double *sigma_max) {
+    const int32_t *ww = weighted ? w : NULL;
+    double *delta_all = (double *)malloc((size_t)nq * (size_t)n * sizeof(double));
+    if (!delta_all) return -2;
+    int rc = 0;
+    double smax = 0.0;
+#pragma omp parallel reduction(| : rc) reduction(max : smax)
+    {
+        uint32_t *dist = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+        double *sigma = (double *)malloc((size_t)n * sizeof(double));
+        dvent *ord = (dvent *)malloc((size_t)n * sizeof(dvent));
+        if (!dist || !sigma || !ord) rc |= 2;
+#pragma omp for schedule(dynamic, 1)
+        for (int32_t q = 0; q < nq; ++q) {
+            if (rc & 2) continue;
+            if (srcs[q] < 0 || srcs[q] >= n) { rc |= 4; continue; }
+            const int r0 = ww ? orc_sssp(n, row_ptr, col, ww, srcs[q], dist) : orc_bfs(n, row_ptr, col, srcs[q], dist);
+            if (r0 != 0) { rc |= 8; continue; }
+            const int r = bc_one(n, row_ptr, col, ww, srcs[q], dist, sigma, delta_all + (size_t)q * (size_t)n, ord);
+            if (r < 0) { rc |= 16; continue; }
+            rc |= r;
+            for (int64_t v = 0; v < n; ++v) if (sigma[v] > smax) smax = sigma[v];
+        }
+        free(dist); free(sigma); free(ord);
+    }
+    if (rc & ~1) { free(delta_all); return -1 - (rc & ~1); }
+    for (int64_t v = 0; v < n; ++v) {
+        double acc = 0.0;
+        for (int32_t q = 0; q < nq; ++q)
+            if (srcs[q] != v) acc = acc + delta_all[(size_t)q * (size_t)n + (size_t)v];
+        bc[v] = acc;
+    }
+    free(delta_all);
+    if (sigma_max) *sigma_max = smax;
+    return rc & 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* landmark labeling query (LL)                                              */
+/* ------------------------------------------------------------------------ */
+/* labels: vertex-major uint32[n][K], labels[v * K + k] = d(s_k, v), UINT32_MAX
+   = unreachable. pairs: int32[2 * Q] (u, v). out[i] = min over k with both
+   entries finite of labels[u][k] + labels[v][k] (exact in uint64), UINT64_MAX
+   when no landmark reaches both. Returns 0, or -1 on a vertex id out of range. */
+int orc_ll_query(int64_t n, int32_t K, const uint32_t *labels, int64_t Q, const int32_t *pairs, uint64_t *out) {
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+    for (int64_t i = 0; i < Q; ++i) {
+        const int32_t u = pairs[2 * i], v = pairs[2 * i + 1];
+        if (u < 0 || u >= n || v < 0 || v >= n) { bad |= 1; out[i] = UINT64_MAX; continue; }
+        const uint32_t *lu = labels + (size_t)u * (size_t)K, *lv = labels + (size_t)v * (size_t)K;
+        uint64_t best = UINT64_MAX;
+        for (int32_t k = 0; k < K; ++k) {
+            if (g_mutation != 7 && (lu[k] == UINT32_MAX || lv[k] == UINT32_MAX)) continue;  /* planted 7: no reach check */
+            const uint64_t d = (uint64_t)lu[k] + (uint64_t)lv[k];
+            if (d < best) best = d;
+        }
+        out[i] = best;
     }
     return bad ? -1 : 0;
 }
