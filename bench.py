@@ -63,6 +63,17 @@ def parse():
     ap.add_argument("--serve-lambdas", default="2000,5000,10000,20000,50000")
     ap.add_argument("--configs", action="store_true",
                     help="only the other workloads (R-MAT s14 plain, s22 PPR, s24 SSSP) with their baselines")
+    ap.add_argument("--ncp", action="store_true",
+                    help="only the NCP application: PPRs from 0.01%% of R-MAT s22, sweep cuts, profile")
+    ap.add_argument("--ncp-scale", type=int, default=22, help="R-MAT scale of the NCP run (22 = the PPR workload)")
+    ap.add_argument("--ncp-top", type=int, default=4096, help="vertices per sweep")
+    ap.add_argument("--bc", action="store_true",
+                    help="only the BC application: 100 sampled sources, SSSP on the grid and BFS on R-MAT s22")
+    ap.add_argument("--bc-sources", type=int, default=100, help="sampled sources per BC run")
+    ap.add_argument("--ll", action="store_true",
+                    help="only the LL application: 1,024 SSSPs on the grid, labels, 2^20 distance queries")
+    ap.add_argument("--ll-pairs", type=int, default=1 << 20, help="pairs per query batch of the LL run")
+    ap.add_argument("--ll-landmarks", type=int, default=NQ, help="landmarks of the LL run (1,024 = the workload)")
     ap.add_argument("--ablation", action="store_true",
                     help="only the scheduling / yield / partition-size ablation on the bench workload")
     return ap.parse_args()
@@ -381,6 +392,256 @@ def run_ablation(args):
     print(json.dumps({"metric": "ablation", "workload": WORKLOAD, "sources": nq, "rows": rows}), flush=True)
 
 
+def run_ncp(args):
+    """NCP application (Sec. 1, 6.1): PPRs from 0.01% of the vertices of R-MAT s22
+    (alpha 0.15, eps 1e-7), each swept to --ncp-top vertices, and the profile =
+    best conductance per cluster size. One JSON line: PPR and sweep times, the
+    sweep kernel's HBM roofline, sampled bit-exact parity, the CPU oracle's sweep."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda:0")
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    from paper_2103_14915_gb300 import fg, inputs
+    alpha, eps, top = 0.15, 1e-7, args.ncp_top
+    if args.ncp_scale == 22:
+        name, g = "rmat22_ncp", inputs.workload_graph("rmat22_ppr")
+    else:
+        name, g = f"rmat{args.ncp_scale}_ncp", inputs.rmat(args.ncp_scale, 16, seed=args.ncp_scale)
+    st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, fg.fg_default_graph_opts())
+    fg.check(st)
+    seeds = inputs.ncp_seeds(g)
+    nq = len(seeds)
+    s_d = torch.from_numpy(seeds).to(dev)
+    p = torch.empty((nq, g.n), dtype=torch.float32, device=dev)
+    order = torch.empty((nq, top), dtype=torch.int32, device=dev)
+    phi = torch.empty((nq, top), dtype=torch.float64, device=dev)
+    count = torch.empty(nq, dtype=torch.int32, device=dev)
+    ncp = torch.empty(top, dtype=torch.float64, device=dev)
+    o = fg.fg_default_opts()
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        fn()
+        b.record()
+        fg.check(fg.fg_sync(stream))
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    ppr = lambda: fg.check(fg.fg_ppr_batch(h, s_d, nq, alpha, eps, p, None, None, stream, o))
+    sweep = lambda: fg.check(fg.fg_ncp_sweep(h, p, nq, top, order, phi, count, ncp, False, stream))
+    fg.check(fg.fg_ppr_batch(h, s_d[:64], 64, alpha, eps, p, None, None, stream, o))
+    t_ppr = timed(ppr)
+    for _ in range(2):
+        sweep()  # the first call builds the degree table
+    t_sweeps = sorted(timed(sweep) for _ in range(max(3, args.steps)))
+    t_sweep = t_sweeps[len(t_sweeps) // 2]
+    # algorithmic bytes: each PPR row once (4 B per vertex) plus the degree table once
+    alg_bytes = 4 * g.n * nq + 4 * g.n
+    achieved = alg_bytes / (t_sweep / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    prof = ncp.cpu().numpy()
+    cnt = count.cpu().numpy()
+    # parity and the CPU baseline on the oracle's own PPR rows (FP64 push rounded to FP32) for
+    # a sample of the seeds: the GPU sweep of those rows against the oracle's sweep, bit for bit
+    k_cpu = min(nq, 32)
+    rows_o = np.stack([oracle.ppr_push(g, int(s), alpha, eps)[0] for s in seeds[:k_cpu]]).astype(np.float32)
+    t0 = time.perf_counter()
+    ro, rph, rc = oracle.ncp_sweep(g, rows_o, top)
+    t_cpu = time.perf_counter() - t0
+    po = torch.from_numpy(rows_o).to(dev)
+    fg.check(fg.fg_ncp_sweep(h, po, k_cpu, top, order[:k_cpu], phi[:k_cpu], count[:k_cpu], None, False, stream))
+    fg.check(fg.fg_sync(stream))
+    exact = bool(np.array_equal(order[:k_cpu].cpu().numpy(), ro) and np.array_equal(count[:k_cpu].cpu().numpy(), rc)
+                 and np.array_equal(phi[:k_cpu].cpu().numpy(), rph, equal_nan=True))
+    finite = np.isfinite(prof)
+    kbest = int(np.argmin(np.where(finite, prof, np.inf)))
+    points = {str(k): float(prof[k - 1]) for k in (1, 10, 100, 1000, top) if k <= top and finite[k - 1]}
+    res = {"metric": "NCP application", "workload": name, "n": g.n, "m": g.m, "seeds": nq,
+           "seed_fraction": 1e-4, "alpha": alpha, "eps": eps, "top": top, "data": "synthetic",
+           "ppr_ms": t_ppr, "sweep_ms": t_sweep, "ncp_total_ms": t_ppr + t_sweep,
+           "ppr_per_s": nq / (t_ppr / 1e3), "sweeps_per_s": nq / (t_sweep / 1e3),
+           "sweep_roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                              "frac": achieved / peak, "peak_kind": peak_kind,
+                              "alg_bytes_per_launch": alg_bytes},
+           "exact_sampled": exact, "parity_rows": f"oracle FP64 push rows of the first {k_cpu} seeds",
+           "cpu_oracle_sweeps_per_s": k_cpu / t_cpu, "cpu_sample": k_cpu, "cpu_cores": oracle.num_threads(),
+           "count_min": int(cnt.min()), "count_median": int(np.median(cnt)),
+           "profile": {"best_phi": float(prof[kbest]), "best_size": kbest + 1, "points": points}}
+    fg.fg_graph_destroy(h)
+    print(json.dumps(res), flush=True)
+
+
+def run_bc(args):
+    """BC application (Sec. 1, 6.1): 100 random sources; one SSSP per source on the
+    weighted grid workload, one BFS per source on the R-MAT s22 graph; then the
+    Brandes dependency accumulation on the GPU. One JSON line per run with the
+    batch and BC times, bit-exact parity of every vertex's centrality against the
+    oracle chain (its own Dijkstra / BFS, path counts and dependencies), and the
+    oracle's rate on the host cores."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda:0")
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    from paper_2103_14915_gb300 import fg, inputs
+    stream = torch.cuda.current_stream().cuda_stream
+    for name, weighted in (("grid1024_bfs_sssp", True), ("rmat22_ppr", False)):
+        g = inputs.workload_graph(name)
+        method = fg.FG_PART_GROW if weighted else fg.FG_PART_AUTO
+        st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, fg.fg_default_graph_opts(
+            partition_method=method))
+        fg.check(st)
+        srcs = inputs.sources_uniform(g, args.bc_sources, seed=74)
+        nq = len(srcs)
+        s_d = torch.from_numpy(srcs).to(dev)
+        dist = torch.empty((nq, g.n), dtype=torch.int32, device=dev)
+        bc = torch.empty(g.n, dtype=torch.float64, device=dev)
+        kind = fg.FG_QUERY_SSSP if weighted else fg.FG_QUERY_BFS
+        st, opts, _ = fg.fg_tune_opts(h, kind, s_d, nq, stream)
+        fg.check(st)
+        batch = fg.fg_sssp_batch if weighted else fg.fg_bfs_batch
+
+        def timed(fn):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            out = fn()
+            b.record()
+            torch.cuda.synchronize()
+            return a.elapsed_time(b), out
+
+        def run_bc_kernel():
+            st, info = fg.fg_bc_accumulate(h, s_d, nq, dist, weighted, bc, False, stream)
+            fg.check(st)
+            return info
+
+        fg.check(batch(h, s_d, nq, dist, stream, opts))
+        fg.check(fg.fg_sync(stream))
+        run_bc_kernel()  # scratch allocation and grid sizing happen here
+        t_batch = sorted(timed(lambda: fg.check(batch(h, s_d, nq, dist, stream, opts)))[0]
+                         for _ in range(3))[1]
+        fg.check(fg.fg_sync(stream))
+        runs = [timed(run_bc_kernel) for _ in range(max(3, args.steps))]
+        t_bc = sorted(r[0] for r in runs)[len(runs) // 2]
+        info = runs[-1][1]
+        got = bc.cpu().numpy()
+        t0 = time.perf_counter()
+        ref, smax, exact = oracle.bc(g, srcs, weighted)
+        t_cpu = time.perf_counter() - t0
+        same = bool(np.array_equal(got, ref)) if exact else bool(np.allclose(got, ref, rtol=1e-9))
+        top = np.argsort(-ref)[:5]
+        res = {"metric": "BC application", "workload": f"{name.split('_')[0]}_bc_{'sssp' if weighted else 'bfs'}",
+               "n": g.n, "m": g.m, "sources": nq, "weighted": weighted, "data": "synthetic",
+               "batch_ms": t_batch, "bc_ms": t_bc, "bc_total_ms": t_batch + t_bc,
+               "sources_per_s": nq / ((t_batch + t_bc) / 1e3), "waves": info.waves,
+               "sigma_max": info.sigma_max, "inexact": info.inexact,
+               "batch_opts": {k2: int(getattr(opts, k2)) for k2 in ("sched", "sched_window", "delta")},
+               "parity": "bit-exact, every vertex" if exact else "rtol 1e-9 (a path count passed 2^53)",
+               "matches_oracle": same, "cpu_oracle_sources_per_s": nq / t_cpu, "cpu_cores": oracle.num_threads(),
+               "top_vertices": [int(v) for v in top]}
+        fg.fg_graph_destroy(h)
+        del dist
+        print(json.dumps(res), flush=True)
+
+
+def run_ll(args):
+    """LL application (Sec. 1, 6.1): 1,024 SSSPs from random landmarks on the grid
+    workload, label construction (query-major rows to vertex-major labels) and a
+    batch of distance queries answered from the labels. One JSON line: the three
+    stages' times, the two label kernels' HBM rooflines, sampled bit-exact parity
+    against the oracle chain (its own SSSP rows, labels, queries), the oracle's rates."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda:0")
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    from paper_2103_14915_gb300 import fg, inputs
+    g = inputs.workload_graph(WORKLOAD)
+    lms = inputs.workload_sources(WORKLOAD, g, k=args.ll_landmarks)
+    K, n, Q = len(lms), g.n, args.ll_pairs
+    gopts = fg.fg_default_graph_opts(partition_method=fg.FG_PART_GROW, partition_vertices=args.partition_vertices)
+    st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, gopts)
+    fg.check(st)
+    stream = torch.cuda.current_stream().cuda_stream
+    s_d = torch.from_numpy(lms).to(dev)
+    dist = torch.empty((K, n), dtype=torch.int32, device=dev)
+    lab = torch.empty((n, K), dtype=torch.int32, device=dev)
+    rng = np.random.default_rng(2024)
+    pairs = rng.integers(0, n, size=(Q, 2)).astype(np.int32)
+    pr = torch.from_numpy(pairs).to(dev)
+    est = torch.empty(Q, dtype=torch.int64, device=dev)
+    if args.no_tune:
+        opts = fg.fg_default_opts(**TUNED_SSSP)
+    else:
+        st, opts, _ = fg.fg_tune_opts(h, fg.FG_QUERY_SSSP, s_d, K, stream)
+        fg.check(st)
+
+    def timed(fn, reps):
+        out = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            fn()
+            b.record()
+            fg.check(fg.fg_sync(stream))
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        return sorted(out)[len(out) // 2]
+
+    sssp = lambda: fg.check(fg.fg_sssp_batch(h, s_d, K, dist, stream, opts))
+    build = lambda: fg.check(fg.fg_ll_build_labels(dist, K, n, lab, stream))
+    query = lambda: fg.check(fg.fg_ll_query(lab, n, K, pr, Q, est, stream))
+    t_sssp = timed(sssp, 3)
+    build()
+    query()
+    reps = max(5, args.steps)
+    t_build = timed(build, reps)  # inputs (4 GB each way) far exceed L2: no flush needed
+    t_query = timed(query, reps)
+    peak, peak_kind = measured_peaks()
+    b_build = 8 * K * n
+    b_query = Q * (8 * K + 16)
+    got = est.cpu().numpy().view(np.uint64)
+    vs = rng.choice(n, size=2000, replace=False)
+    lab_s = lab[torch.from_numpy(vs).to(dev)].cpu().numpy().view(np.uint32)
+    del dist
+    # the oracle chain: its own SSSP rows (all landmarks), labels, queries on a sample
+    rows = oracle.sssp(g, lms)
+    t0 = time.perf_counter()
+    ref = oracle.ll_labels(rows)
+    t_cpu_build = time.perf_counter() - t0
+    del rows
+    sample = rng.choice(Q, size=min(Q, 20000), replace=False)
+    t0 = time.perf_counter()
+    ref_est = oracle.ll_query(ref, pairs[sample])
+    t_cpu_query = time.perf_counter() - t0
+    exact = bool(np.array_equal(lab_s, ref[vs]) and np.array_equal(got[sample], ref_est))
+    finite = got[got != np.iinfo(np.uint64).max]
+    res = {"metric": "LL application", "workload": f"grid1024_ll_k{K}", "n": n, "m": g.m, "landmarks": K, "pairs": Q,
+           "data": "synthetic", "sssp_ms": t_sssp, "labels_ms": t_build, "queries_ms": t_query,
+           "ll_total_ms": t_sssp + t_build + t_query, "queries_per_s": Q / (t_query / 1e3),
+           "labels_roofline": {"bound": "hbm", "achieved": b_build / (t_build / 1e3) / 1e9, "peak": peak,
+                               "unit": "GB/s", "frac": b_build / (t_build / 1e3) / 1e9 / peak,
+                               "peak_kind": peak_kind, "alg_bytes_per_launch": b_build},
+           "query_roofline": {"bound": "hbm", "achieved": b_query / (t_query / 1e3) / 1e9, "peak": peak,
+                              "unit": "GB/s", "frac": b_query / (t_query / 1e3) / 1e9 / peak,
+                              "peak_kind": peak_kind, "alg_bytes_per_launch": b_query},
+           "sssp_opts": {k2: int(getattr(opts, k2)) for k2 in ("sched", "sched_window", "delta")},
+           "exact_sampled": exact, "parity_sample": "2,000 vertices' labels, 20,000 pairs",
+           "cpu_oracle_labels_s": t_cpu_build, "cpu_oracle_queries_per_s": len(sample) / t_cpu_query,
+           "cpu_cores": oracle.num_threads(),
+           "estimate_mean": float(finite.mean()) if finite.size else None}
+    fg.fg_graph_destroy(h)
+    print(json.dumps(res), flush=True)
+
+
 def run_configs(args):
     """The other workloads (R-MAT s14 plain SSSP, R-MAT s22 PPR, R-MAT s24 SSSP): buffered engine,
     plain per-query GPU form and the CPU oracle on the host cores, one JSON line."""
@@ -510,6 +771,15 @@ def main():
         return
     if args.ablation:
         run_ablation(args)
+        return
+    if args.ncp:
+        run_ncp(args)
+        return
+    if args.ll:
+        run_ll(args)
+        return
+    if args.bc:
+        run_bc(args)
         return
     if args.configs:
         run_configs(args)

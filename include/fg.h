@@ -323,6 +323,110 @@ fg_status fg_server_release(fg_server *s, uint64_t id);
 fg_status fg_sssp_batch_noalloc(const fg_graph *g, const int32_t *src, int32_t nq, uint32_t *dist_out,
                                 void *stream);
 
+/*
+ * Sweep cuts over PPR vectors: the conductance step of the network community
+ * profile (NCP) application, which runs PPRs from randomly chosen seed
+ * vertices and keeps, for each cluster size, the best conductance found
+ * (Sec. 1; Sec. 6.1 seeds 0.01% of the vertices).
+ *
+ * For each query q (row q of p, as fg_ppr_batch writes it: float[nq * n],
+ * original vertex order) the vertices with p(v) > 0 are ordered by the FP32
+ * key p(v) / max(d(v), 1), largest first, ties by smaller id; d = out-degree.
+ * For each prefix S_k (k = 1 .. count) of the first `top` vertices:
+ *   phi(S_k) = cut(S_k) / min(vol(S_k), vol(V) - vol(S_k))  (FP64; 1.0 when
+ *   that minimum is 0), vol = sum of out-degrees (vol(V) = m), cut = arcs from
+ *   S_k to the rest, computed as sum over v in S_k of d(v) - 2 * (arcs from v
+ *   to vertices placed before v), exact for a graph stored with both arcs of
+ *   every edge; on a directed graph the same formula is evaluated.
+ *
+ * Outputs (DEVICE pointers owned by the caller; any may be NULL, not all):
+ *   order_out  int32[nq * top]: order_out[q * top + k] = the (k+1)-th vertex
+ *              (original id); -1 past count
+ *   phi_out    double[nq * top]: phi(S_{k+1}); NaN past count
+ *   count_out  int32[nq]: min(top, number of vertices with p(v) > 0)
+ *   ncp_out    double[top]: ncp_out[k] = min over this call's queries of
+ *              phi(S_{k+1}), +inf where no query has k+1 vertices; with
+ *              accumulate != 0 the minimum also takes the values already in
+ *              ncp_out (profile over several calls).
+ * Requires 1 <= top <= FG_NCP_MAX_TOP and nq >= 1; p 4-byte aligned, phi_out
+ * and ncp_out 8-byte aligned; the graph's device must be current.
+ *
+ * Asynchronous on `stream`, with one exception: the first call on a graph
+ * builds the graph's table of out-degrees by original id (4 * n bytes, freed
+ * with the graph) and waits for it. Errors are detected on the host only.
+ */
+#define FG_NCP_MAX_TOP 4096
+fg_status fg_ncp_sweep(fg_graph *g, const float *p, int32_t nq, int32_t top, int32_t *order_out,
+                       double *phi_out, int32_t *count_out, double *ncp_out, int32_t accumulate, void *stream);
+
+/*
+ * Landmark labeling (LL): a batch of SSSP (or BFS) queries from landmark
+ * vertices s_0 .. s_{K-1} gives every vertex a label of K distances, and a
+ * pair of vertices is answered from their two labels alone (Sec. 1; Sec. 6.1
+ * runs 1,024 SSSPs from randomly chosen landmarks).
+ *
+ * fg_ll_build_labels: label construction. dist: the batch's output,
+ * uint32[K * n] query-major (row k = d(s_k, .), UINT32_MAX = unreachable);
+ * labels: uint32[n * K] vertex-major, labels[v * K + k] = d(s_k, v). Both are
+ * DEVICE pointers owned by the caller, 4-byte aligned, not overlapping. The
+ * copy is asynchronous on `stream`; host-detected errors only.
+ */
+fg_status fg_ll_build_labels(const uint32_t *dist, int32_t K, int64_t n, uint32_t *labels, void *stream);
+
+/*
+ * fg_ll_query: distance estimates for Q vertex pairs. labels: uint32[n * K]
+ * as above; pairs: int32[2 * Q] (u, v); est_out: uint64[Q],
+ *   est_out[i] = min over k with labels[u][k], labels[v][k] both finite of
+ *                labels[u][k] + labels[v][k]   (exact in 64 bits),
+ * UINT64_MAX when no landmark reaches both, and for a pair with a vertex id
+ * outside [0, n). On an undirected graph the estimate is an upper bound on
+ * d(u, v), exact when some landmark lies on a shortest u-v path (in particular
+ * when u or v is a landmark). DEVICE pointers owned by the caller (labels and
+ * pairs 4-byte, est_out 8-byte aligned; K a multiple of 4 with 16-byte aligned
+ * labels takes 16-byte loads). Q = 0 is a no-op. Asynchronous on `stream`.
+ */
+fg_status fg_ll_query(const uint32_t *labels, int64_t n, int32_t K, const int32_t *pairs, int64_t Q,
+                      uint64_t *est_out, void *stream);
+
+/*
+ * Betweenness centrality from sampled sources (BC): one SSSP (weighted graph)
+ * or BFS (unweighted graph) per sampled source, then the dependency
+ * accumulation of Brandes (Sec. 1; Sec. 6.1 samples 100 sources).
+ *
+ * dist: the batch's exact rows, uint32[nq * n] in original vertex order, as
+ * fg_sssp_batch (weighted = 1) or fg_bfs_batch (weighted = 0) wrote them for
+ * the sources src (int32[nq]); an arc (u, w) of weight wt (1 when weighted = 0)
+ * is on a shortest path from s when d_s(u) + wt = d_s(w). For every source:
+ *   sigma_s(w) = number of shortest s-w paths (sigma_s(s) = 1),
+ *   delta_s(u) = sum over u's tight out-arcs (u, w), in the order the graph
+ *                lists them, of sigma_s(u) / sigma_s(w) * (1 + delta_s(w)),
+ * each FP64 operation rounded as written. Then, for every vertex v,
+ *   bc[v] = (accumulate ? bc[v] : 0) + sum over q in order, src[q] != v, of delta_{src[q]}(v).
+ * Sampled BC is usually scaled by n / nq; that is left to the caller.
+ *
+ * Requirements: weighted = 1 needs a weighted graph with positive weights
+ * (FG_ERR_UNSUPPORTED otherwise: a weight-0 arc would tie vertices at equal
+ * distance); nq * n < 2^32 (split larger batches; scratch of 32 * nq * n bytes
+ * is kept with the graph). src, dist and bc (double[n]) are DEVICE pointers
+ * owned by the caller. Each dist row must start at its source (d = 0 there):
+ * otherwise FG_ERR_INVALID_ARG (detected on the device).
+ *
+ * info (host, nullable): waves = the longest shortest-path hop count over the
+ * batch plus one; sigma_max = the largest path count; inexact = 1 when a path
+ * count reached 2^53, beyond which FP64 sums of counts may round (the result
+ * is then no longer independent of the order of the atomic additions).
+ *
+ * Synchronous: enqueues on `stream` (after the batch that wrote dist, if it
+ * ran on the same stream), waits, and returns the device status.
+ */
+typedef struct {
+    int32_t waves;
+    int32_t inexact;
+    double sigma_max;
+} fg_bc_info_t;
+fg_status fg_bc_accumulate(fg_graph *g, const int32_t *src, int32_t nq, const uint32_t *dist, int32_t weighted,
+                           double *bc, int32_t accumulate, fg_bc_info_t *info, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

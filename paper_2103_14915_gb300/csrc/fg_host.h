@@ -78,6 +78,15 @@ struct Workspace {
   }
 };
 
+// Scratch of fg_bc_accumulate, grown on demand and kept with the graph.
+struct BcWorkspace {
+  DevBuf pc, sigma, delta, dint, wave, wave_off, ctrl;
+  void release_all() {
+    DevBuf *all[] = {&pc, &sigma, &delta, &dint, &wave, &wave_off, &ctrl};
+    for (DevBuf *b : all) b->release();
+  }
+};
+
 }  // namespace fg
 
 // Graph handle of the C ABI: the partitioned graph on the device, its own
@@ -90,6 +99,10 @@ struct fg_graph {
   bool weighted = false;
   int device = 0;
   fg::DevBuf rp, adj, wt, orig, intl;
+  fg::DevBuf deg;                  // out-degree per original id (built by the first fg_ncp_sweep)
+  fg::BcWorkspace bc;              // fg_bc_accumulate scratch (guarded by mu)
+  bool has_zero_weight = false;    // some arc has weight 0
+  int bc_blocks = 0;               // cooperative grid of the BC kernel (0 = not sized yet)
   size_t graph_bytes = 0;
   std::mutex mu;                   // guards ws, last_done and the cached launch shapes
   cudaEvent_t last_done = nullptr;

@@ -278,7 +278,10 @@ extern "C" fg_status fg_graph_create_ex(int64_t n, int64_t m, const int64_t *row
     if (m > 0) CUDA_TRY_G(cudaMemcpy(g->wt.p, i_wt.data(), sizeof(uint32_t) * (size_t)m, cudaMemcpyHostToDevice));
     g->graph_bytes += sizeof(uint32_t) * (size_t)m;
     double sum = 0.0;
-    for (int64_t e = 0; e < m; ++e) sum += (double)i_wt[(size_t)e];
+    for (int64_t e = 0; e < m; ++e) {
+      sum += (double)i_wt[(size_t)e];
+      if (i_wt[(size_t)e] == 0u) g->has_zero_weight = true;
+    }
     if (m > 0) g->mean_weight = sum / (double)m;
   }
   for (int64_t v = 0; v < n; ++v) g->max_degree = std::max(g->max_degree, i_rp[(size_t)v + 1] - i_rp[(size_t)v]);
@@ -323,6 +326,8 @@ extern "C" fg_status fg_graph_destroy(fg_graph *g) {
     }
     g->ws.release_all();
     g->rp.release(); g->adj.release(); g->wt.release(); g->orig.release(); g->intl.release();
+    g->deg.release();
+    g->bc.release_all();
     if (g->last_done) cudaEventDestroy(g->last_done);
   }
   delete g;

@@ -81,6 +81,10 @@ class fg_request_info(ctypes.Structure):
                 ("mass", ctypes.c_double)]
 
 
+class fg_bc_info_t(ctypes.Structure):
+    _fields_ = [("waves", ctypes.c_int32), ("inexact", ctypes.c_int32), ("sigma_max", ctypes.c_double)]
+
+
 class fg_graph_info_t(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("partition_vertices", ctypes.c_int32),
                 ("num_partitions", ctypes.c_int32), ("partition_method", ctypes.c_int32),
@@ -91,9 +95,11 @@ EXPORTS = ("fg_default_opts", "fg_default_graph_opts", "fg_graph_create", "fg_gr
            "fg_graph_destroy", "fg_graph_info", "fg_sssp_batch", "fg_bfs_batch", "fg_ppr_batch", "fg_sync",
            "fg_last_error", "fg_stats", "fg_partition_plan", "fg_sssp_batch_noalloc", "fg_default_server_opts",
            "fg_server_create", "fg_server_destroy", "fg_server_submit", "fg_server_poll", "fg_server_info",
-           "fg_server_release", "fg_tune_opts")
+           "fg_server_release", "fg_tune_opts", "fg_ncp_sweep", "fg_ll_build_labels", "fg_ll_query",
+           "fg_bc_accumulate")
 
 FG_NOALLOC_MAX_VERTICES = 1 << 20
+FG_NCP_MAX_TOP = 4096
 
 
 def lib_path() -> Path:
@@ -126,6 +132,10 @@ def load():
     lib.fg_stats.argtypes = [vp, ctypes.POINTER(fg_stats_t)]
     lib.fg_partition_plan.argtypes = [i64, vp, vp, i32, i32, vp]
     lib.fg_sssp_batch_noalloc.argtypes = [vp, vp, i32, vp, vp]
+    lib.fg_ncp_sweep.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, i32, vp]
+    lib.fg_ll_build_labels.argtypes = [vp, i32, i64, vp, vp]
+    lib.fg_ll_query.argtypes = [vp, i64, i32, vp, i64, vp, vp]
+    lib.fg_bc_accumulate.argtypes = [vp, vp, i32, vp, i32, vp, i32, ctypes.POINTER(fg_bc_info_t), vp]
     lib.fg_tune_opts.argtypes = [vp, i32, vp, i32, vp, ctypes.POINTER(fg_opts), ctypes.POINTER(fg_tune_report)]
     u64p = ctypes.POINTER(ctypes.c_uint64)
     lib.fg_default_server_opts.argtypes = [ctypes.POINTER(fg_server_opts)]
@@ -139,7 +149,7 @@ def load():
     for name in ("fg_graph_create", "fg_graph_create_ex", "fg_graph_destroy", "fg_graph_info", "fg_sssp_batch",
                  "fg_bfs_batch", "fg_ppr_batch", "fg_sync", "fg_stats", "fg_partition_plan",
                  "fg_sssp_batch_noalloc", "fg_server_create", "fg_server_destroy", "fg_server_submit",
-                 "fg_server_poll", "fg_server_info", "fg_server_release", "fg_tune_opts"):
+                 "fg_server_poll", "fg_server_info", "fg_server_release", "fg_tune_opts", "fg_ncp_sweep", "fg_ll_build_labels", "fg_ll_query"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -258,6 +268,31 @@ def fg_partition_plan(n, row_ptr, col, method, partition_vertices, perm_out) -> 
 def fg_sssp_batch_noalloc(g, src, nq, dist_out, stream=None) -> int:
     """Synchronous; device pointers only; graph of at most FG_NOALLOC_MAX_VERTICES vertices."""
     return load().fg_sssp_batch_noalloc(g, _ptr(src), nq, _ptr(dist_out), _stream(stream))
+
+
+def fg_ncp_sweep(g, p, nq, top, order_out=None, phi_out=None, count_out=None, ncp_out=None, accumulate=False,
+                 stream=None) -> int:
+    """Sweep cuts over PPR rows p (device float[nq, n]); outputs are device tensors or None."""
+    return load().fg_ncp_sweep(g, _ptr(p), nq, top, _ptr(order_out), _ptr(phi_out), _ptr(count_out), _ptr(ncp_out),
+                               1 if accumulate else 0, _stream(stream))
+
+
+def fg_ll_build_labels(dist, K, n, labels, stream=None) -> int:
+    """Landmark labels: dist uint32[K, n] (query-major) -> labels uint32[n, K] (vertex-major), device tensors."""
+    return load().fg_ll_build_labels(_ptr(dist), K, n, _ptr(labels), _stream(stream))
+
+
+def fg_ll_query(labels, n, K, pairs, Q, est_out, stream=None) -> int:
+    """Landmark distance estimates for Q pairs (device int32[Q, 2]) into est_out (device uint64 / int64[Q])."""
+    return load().fg_ll_query(_ptr(labels), n, K, _ptr(pairs), Q, _ptr(est_out), _stream(stream))
+
+
+def fg_bc_accumulate(g, src, nq, dist, weighted, bc, accumulate=False, stream=None):
+    """Brandes dependencies of the batch's rows summed into bc (device double[n]); returns (status, fg_bc_info_t)."""
+    info = fg_bc_info_t()
+    st = load().fg_bc_accumulate(g, _ptr(src), nq, _ptr(dist), 1 if weighted else 0, _ptr(bc), 1 if accumulate else 0,
+                                 ctypes.byref(info), _stream(stream))
+    return st, info
 
 
 def fg_default_server_opts(**overrides) -> fg_server_opts:

@@ -201,6 +201,12 @@ def sources_logdeg(g: Graph, k: int, seed: int) -> np.ndarray:
     return out[:k].copy()
 
 
+
+def ncp_seeds(g: Graph, fraction: float = 1e-4, seed: int = 7) -> np.ndarray:
+    """PPR seeds of the NCP application: round(fraction * n) distinct vertices,
+    uniform among those with out-degree >= 1 (Sec. 6.1 seeds 0.01% of V)."""
+    return sources_uniform(g, max(1, round(fraction * g.n)), seed)
+
 # ---------------------------------------------------------------------------
 # The five workloads (sizes from the paper's applications: LL runs 1,024
 # SSSPs, BC ~100 sources, NCP thousands of PPRs; Sec. 6.1).

@@ -155,3 +155,26 @@ def test_partition_plan_bad_args(lib):
     perm = np.empty(4, dtype=np.int32)
     assert fg.fg_partition_plan(4, None, None, fg.FG_PART_GROW, 2, perm) == fg.FG_ERR_INVALID_ARG
     assert fg.fg_partition_plan(4, None, None, 9, 2, perm) == fg.FG_ERR_INVALID_ARG
+
+
+def test_application_entry_points_reject_bad_arguments_on_the_host(lib):
+    """The NCP sweep, landmark labeling and BC entry points check their
+    arguments before any CUDA call (so these run without a GPU)."""
+    p = np.zeros(4, dtype=np.float32)
+    cnt = np.zeros(1, dtype=np.int32)
+    assert fg.fg_ncp_sweep(None, p, 1, 4, None, None, cnt) == fg.FG_ERR_INVALID_ARG
+    lab = np.zeros(16, dtype=np.uint32)
+    pairs = np.zeros(2, dtype=np.int32)
+    est = np.zeros(1, dtype=np.uint64)
+    assert fg.fg_ll_build_labels(None, 4, 4, lab) == fg.FG_ERR_INVALID_ARG
+    assert fg.fg_ll_build_labels(lab, 0, 4, lab) == fg.FG_ERR_INVALID_ARG
+    assert fg.fg_ll_build_labels(lab, 4, 0, lab) == fg.FG_ERR_INVALID_ARG
+    assert fg.fg_ll_query(lab, 4, 4, pairs, -1, est) == fg.FG_ERR_INVALID_ARG
+    assert fg.fg_ll_query(lab, 4, 0, pairs, 1, est) == fg.FG_ERR_INVALID_ARG
+    assert fg.fg_ll_query(None, 4, 4, pairs, 1, est) == fg.FG_ERR_INVALID_ARG
+    assert fg.fg_ll_query(lab, 4, 4, pairs, 0, est) == fg.FG_OK  # empty batch: nothing to launch
+    src = np.zeros(1, dtype=np.int32)
+    bc = np.zeros(4, dtype=np.float64)
+    st, _ = fg.fg_bc_accumulate(None, src, 1, lab, True, bc)
+    assert st == fg.FG_ERR_INVALID_ARG
+    assert ctypes.sizeof(fg.fg_bc_info_t) == 16
