@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--bc", action="store_true",
                     help="only the BC application: 100 sampled sources, SSSP on the grid and BFS on R-MAT s22")
     ap.add_argument("--bc-sources", type=int, default=100, help="sampled sources per BC run")
+    ap.add_argument("--bc-graphs", default="grid,rmat", help="BC runs to do: grid (SSSP), rmat (BFS)")
+    ap.add_argument("--walks", action="store_true",
+                    help="only the query types without a batch engine form: random walks and DFS")
     ap.add_argument("--ll", action="store_true",
                     help="only the LL application: 1,024 SSSPs on the grid, labels, 2^20 distance queries")
     ap.add_argument("--ll-pairs", type=int, default=1 << 20, help="pairs per query batch of the LL run")
@@ -491,7 +494,8 @@ def run_bc(args):
     import oracle
     from paper_2103_14915_gb300 import fg, inputs
     stream = torch.cuda.current_stream().cuda_stream
-    for name, weighted in (("grid1024_bfs_sssp", True), ("rmat22_ppr", False)):
+    runs = {"grid": ("grid1024_bfs_sssp", True), "rmat": ("rmat22_ppr", False)}
+    for name, weighted in (runs[k] for k in args.bc_graphs.split(",")):
         g = inputs.workload_graph(name)
         method = fg.FG_PART_GROW if weighted else fg.FG_PART_AUTO
         st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, fg.fg_default_graph_opts(
@@ -548,6 +552,84 @@ def run_bc(args):
         fg.fg_graph_destroy(h)
         del dist
         print(json.dumps(res), flush=True)
+
+
+def run_walks(args):
+    """Random-walk and DFS queries (query types of the framework, Sec. 3). Walks:
+    2^20 walks of 80 steps from uniform sources on R-MAT s22. DFS: 1,024 queries
+    on R-MAT s18. One JSON line each with the GPU time, bit-exact parity of every
+    output against the oracle, and the oracle's rate on the host cores."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda:0")
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    from paper_2103_14915_gb300 import fg, inputs
+    stream = torch.cuda.current_stream().cuda_stream
+    peak, peak_kind = measured_peaks()
+
+    def timed(fn, reps):
+        out = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        return sorted(out)[len(out) // 2]
+
+    # random walks
+    g = inputs.workload_graph("rmat22_ppr")
+    st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, fg.fg_default_graph_opts())
+    fg.check(st)
+    nw, L, seed = 1 << 20, 80, 2021
+    srcs = np.random.default_rng(5).integers(0, g.n, size=nw).astype(np.int32)
+    s_d = torch.from_numpy(srcs).to(dev)
+    paths = torch.empty((nw, L + 1), dtype=torch.int32, device=dev)
+    walk = lambda: fg.check(fg.fg_rw_batch(h, s_d, nw, L, seed, paths, stream))
+    walk()
+    t = timed(walk, max(5, args.steps))
+    got = paths.cpu().numpy()
+    t0 = time.perf_counter()
+    ref = oracle.rw(g, srcs, L, seed)
+    t_cpu = time.perf_counter() - t0
+    steps = nw * L
+    alg = nw * (L + 1) * 4 + steps * 12  # the paths written + per step the arc range and the chosen arc
+    print(json.dumps({
+        "metric": "random walks", "workload": "rmat22_rw", "n": g.n, "m": g.m, "walks": nw, "length": L,
+        "data": "synthetic", "ms": t, "steps_per_s": steps / (t / 1e3), "walks_per_s": nw / (t / 1e3),
+        "roofline": {"bound": "hbm (latency of dependent gathers)", "achieved": alg / (t / 1e3) / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": alg / (t / 1e3) / 1e9 / peak, "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": alg},
+        "exact": bool(np.array_equal(got, ref)), "cpu_oracle_steps_per_s": steps / t_cpu,
+        "cpu_cores": oracle.num_threads()}), flush=True)
+    del paths
+    fg.fg_graph_destroy(h)
+
+    # DFS
+    g = inputs.rmat(18, 16, seed=18)
+    st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, fg.fg_default_graph_opts())
+    fg.check(st)
+    nq = 1024
+    srcs = inputs.sources_uniform(g, nq, seed=6)
+    s_d = torch.from_numpy(srcs).to(dev)
+    disc = torch.empty((nq, g.n), dtype=torch.int32, device=dev)
+    dfs = lambda: fg.check(fg.fg_dfs_batch(h, s_d, nq, disc, stream))
+    dfs()
+    t = timed(dfs, 3)
+    got = disc.cpu().numpy().view(np.uint32)
+    t0 = time.perf_counter()
+    ref = oracle.dfs(g, srcs)
+    t_cpu = time.perf_counter() - t0
+    print(json.dumps({
+        "metric": "DFS queries", "workload": "rmat18_dfs", "n": g.n, "m": g.m, "queries": nq, "data": "synthetic",
+        "ms": t, "queries_per_s": nq / (t / 1e3), "exact": bool(np.array_equal(got, ref)),
+        "cpu_oracle_queries_per_s": nq / t_cpu, "cpu_cores": oracle.num_threads(),
+        "bound": "latency: one dependent step chain per query, one warp per query"}), flush=True)
+    fg.fg_graph_destroy(h)
 
 
 def run_ll(args):
@@ -780,6 +862,9 @@ def main():
         return
     if args.bc:
         run_bc(args)
+        return
+    if args.walks:
+        run_walks(args)
         return
     if args.configs:
         run_configs(args)

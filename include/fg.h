@@ -427,6 +427,38 @@ typedef struct {
 fg_status fg_bc_accumulate(fg_graph *g, const int32_t *src, int32_t nq, const uint32_t *dist, int32_t weighted,
                            double *bc, int32_t accumulate, fg_bc_info_t *info, void *stream);
 
+/*
+ * Random-walk queries (RW, one of the framework's query types next to BFS,
+ * SSSP, PPR and DFS; Sec. 3). Walk q starts at src[q] and takes `length`
+ * steps: from vertex u it moves to the (r mod d(u))-th out-neighbour of u,
+ * counting u's arcs in the order the graph was given, where r is output
+ * number 2^32 * q + t + 1 (t = 0 .. length - 1 the step) of a SplitMix64
+ * stream whose state starts at `seed` (Steele, Lea, Flood 2014: the state
+ * advances by 0x9E3779B97F4A7C15 per output, which is mixed with shifts 30,
+ * 27, 31 and multipliers 0xBF58476D1CE4E5B9, 0x94D049BB133111EB). A vertex
+ * without out-arcs ends the walk.
+ *
+ * paths_out: int32[nq * (length + 1)] walk-major, paths_out[q * (length + 1) + t]
+ * = the vertex after t steps (t = 0: src[q]), -1 once the walk has ended or
+ * for a source id outside [0, n). src and paths_out are DEVICE pointers owned
+ * by the caller. Asynchronous on `stream`; host-detected errors only.
+ */
+fg_status fg_rw_batch(const fg_graph *g, const int32_t *src, int32_t nq, int32_t length, uint64_t seed,
+                      int32_t *paths_out, void *stream);
+
+/*
+ * Depth-first search queries (DFS, one of the framework's query types; Sec. 3):
+ * query q is the recursive preorder from src[q], visiting out-neighbours in
+ * the order the graph lists them. disc_out: uint32[nq * n], original vertex
+ * order, disc_out[q * n + v] = the rank at which v is discovered (0 for the
+ * source), UINT32_MAX = not reached. src and disc_out are DEVICE pointers
+ * owned by the caller. Scratch of 8 * nq * n bytes (12 * nq * n on a
+ * relabelled graph) is kept with the graph. Synchronous: enqueues on `stream`,
+ * waits, and returns FG_ERR_INVALID_ARG when a source id is outside [0, n)
+ * (that query's row is left all UINT32_MAX).
+ */
+fg_status fg_dfs_batch(fg_graph *g, const int32_t *src, int32_t nq, uint32_t *disc_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,6 +62,10 @@ def _load():
         lib.orc_ncp_sweep_batch.argtypes = [i64, p, p, i32, p, i32, p, p, p]
         lib.orc_ll_query.argtypes = [i64, i32, p, i64, p, p]
         lib.orc_bc_batch.argtypes = [i64, p, p, p, ctypes.c_int, i32, p, p, p]
+        lib.orc_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        lib.orc_splitmix64.restype = ctypes.c_uint64
+        lib.orc_rw_batch.argtypes = [i64, p, p, i32, p, i32, ctypes.c_uint64, p]
+        lib.orc_dfs_batch.argtypes = [i64, p, p, i32, p, p]
         lib.orc_certificate_batch.restype = i64
         _lib = lib
     return _lib
@@ -89,7 +93,8 @@ def set_mutation(k: int) -> None:
     """Plant a known mistake (tests only): 1 ignore weights, 2 skip last arc,
     3 BFS levels start at 1, 4 PPR transposed operand, 5 PPR drops dangling mass,
     6 sweep counts internal arcs once, 7 LL query ignores unreachable landmarks' sentinel,
-    8 BC dependency drops the 1 of (1 + delta(w))."""
+    8 BC dependency drops the 1 of (1 + delta(w)), 9 random walks draw output k - 1,
+    10 DFS scans each vertex's neighbours from the last arc."""
     _load().orc_set_mutation(int(k))
 
 
@@ -221,3 +226,31 @@ def bc(g, srcs, weighted: bool):
     if r < 0:
         raise ValueError(f"orc_bc_batch failed ({r})")
     return out, float(smax[0]), r == 0
+
+
+def splitmix64(seed: int, k: int) -> int:
+    """Output number k (>= 1) of the SplitMix64 stream whose state starts at seed."""
+    return int(_load().orc_splitmix64(seed & ((1 << 64) - 1), k))
+
+
+def rw(g, srcs, length: int, seed: int) -> np.ndarray:
+    """Random walks: int32[nq, length + 1], -1 after a vertex without out-arcs."""
+    lib = _load()
+    rp, col, _ = _csr(g)
+    srcs = np.ascontiguousarray(np.atleast_1d(srcs), dtype=np.int32)
+    out = np.empty((srcs.size, length + 1), dtype=np.int32)
+    r = lib.orc_rw_batch(g.n, _p(rp), _p(col), srcs.size, _p(srcs), int(length), seed & ((1 << 64) - 1), _p(out))
+    if r != 0:
+        raise ValueError("source out of range")
+    return out
+
+
+def dfs(g, srcs) -> np.ndarray:
+    """DFS discovery ranks, uint32[nq, n] (UINT32_MAX = not reached)."""
+    lib = _load()
+    rp, col, _ = _csr(g)
+    srcs = np.ascontiguousarray(np.atleast_1d(srcs), dtype=np.int32)
+    out = np.empty((srcs.size, g.n), dtype=np.uint32)
+    if lib.orc_dfs_batch(g.n, _p(rp), _p(col), srcs.size, _p(srcs), _p(out)) != 0:
+        raise ValueError("source out of range or allocation failed")
+    return out

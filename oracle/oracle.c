@@ -42,6 +42,17 @@
  *                 bc(v) = sum over sources s != v, in batch order, of delta_s(v).
  *                 Each operation is one IEEE double operation in that order
  *                 (built with -ffp-contract=off: no fused multiply-add).
+ *   orc_dfs       depth-first search (DFS, a query type of the framework,
+ *                 Sec. 3): recursive preorder from s, out-neighbours in CSR
+ *                 order; disc[v] = the rank at which v is discovered
+ *                 (UINT32_MAX = not reached). Written with an explicit stack
+ *                 of (vertex, next arc) pairs, which visits the same order.
+ *   orc_rw_batch  random-walk queries (RW, a query type of the framework,
+ *                 Sec. 3): a walk of L steps from s moves to the
+ *                 (r mod d(u))-th out-neighbour of u in CSR order, r the
+ *                 counter-based SplitMix64 output number 2^32 * walk + step + 1
+ *                 of the stream seeded with `seed` (Steele, Lea and Flood,
+ *                 2014); a vertex without out-arcs ends the walk (-1 after).
  *   orc_ll_query  landmark labeling (LL, Sec. 1, 6.1: labels from a batch of
  *                 SSSPs from landmark vertices): with labels[v][k] = d(s_k, v),
  *                 the distance estimate of a pair (u, v) is the minimum over
@@ -539,6 +550,100 @@ int orc_bc_batch(int64_t n, const int64_t *row_ptr, const int32_t *col, const in
     free(delta_all);
     if (sigma_max) *sigma_max = smax;
     return rc & 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* depth-first search (DFS)                                                  */
+/* ------------------------------------------------------------------------ */
+int orc_dfs(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t src, uint32_t *disc) {
+    if (src < 0 || src >= n) return -1;
+    int32_t *stk_v = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int64_t *stk_e = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    if (!stk_v || !stk_e) { free(stk_v); free(stk_e); return -2; }
+    for (int64_t v = 0; v < n; ++v) disc[v] = UINT32_MAX;
+    uint32_t time = 0;
+    int64_t top = 0;
+    disc[src] = time++;
+    stk_v[0] = src;
+    stk_e[0] = row_ptr[src];
+    while (top >= 0) {
+        const int32_t u = stk_v[top];
+        int64_t e = stk_e[top];
+        const int64_t e_end = row_ptr[u + 1];
+        /* planted 10: the neighbours are scanned from the last arc backwards */
+        if (g_mutation == 10) {
+            int64_t k = e;  /* here e counts the arcs already scanned from the end */
+            while (k < e_end && disc[col[e_end - 1 - (k - row_ptr[u])]] != UINT32_MAX) ++k;
+            if (k < e_end) {
+                const int32_t w = col[e_end - 1 - (k - row_ptr[u])];
+                stk_e[top] = k + 1;
+                disc[w] = time++;
+                ++top;
+                stk_v[top] = w;
+                stk_e[top] = row_ptr[w];
+            } else {
+                --top;
+            }
+            continue;
+        }
+        while (e < e_end && disc[col[e]] != UINT32_MAX) ++e;
+        if (e < e_end) {
+            const int32_t w = col[e];
+            stk_e[top] = e + 1;      /* resume after this arc when w is finished */
+            disc[w] = time++;
+            ++top;
+            stk_v[top] = w;
+            stk_e[top] = row_ptr[w];
+        } else {
+            --top;                   /* every neighbour of u is discovered: u is finished */
+        }
+    }
+    free(stk_v);
+    free(stk_e);
+    return 0;
+}
+
+int orc_dfs_batch(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t nq, const int32_t *srcs,
+                  uint32_t *disc) {
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (int32_t q = 0; q < nq; ++q)
+        if (orc_dfs(n, row_ptr, col, srcs[q], disc + (size_t)q * (size_t)n) != 0) bad |= 1;
+    return bad ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* random walks (RW)                                                         */
+/* ------------------------------------------------------------------------ */
+/* Output number k (k >= 1) of a SplitMix64 stream whose state starts at seed:
+   the state after k steps of the golden gamma, through the mix function. */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t k) {
+    uint64_t z = seed + k * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* paths: int32[nq][L + 1], paths[q][0] = srcs[q]. Returns 0, or -1 on a bad source. */
+int orc_rw_batch(int64_t n, const int64_t *row_ptr, const int32_t *col, int32_t nq, const int32_t *srcs,
+                 int32_t L, uint64_t seed, int32_t *paths) {
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+    for (int32_t q = 0; q < nq; ++q) {
+        int32_t *row = paths + (size_t)q * (size_t)(L + 1);
+        int32_t u = srcs[q];
+        if (u < 0 || u >= n) { bad |= 1; continue; }
+        row[0] = u;
+        for (int32_t t = 0; t < L; ++t) {
+            const int64_t d = u >= 0 ? row_ptr[u + 1] - row_ptr[u] : 0;
+            if (d == 0) { u = -1; row[t + 1] = -1; continue; }
+            const uint64_t k = ((uint64_t)(uint32_t)q << 32) + (uint64_t)t + (g_mutation == 9 ? 0u : 1u);  /* planted 9 */
+            const uint64_t r = orc_splitmix64(seed, k);
+            u = col[row_ptr[u] + (int64_t)(r % (uint64_t)d)];
+            row[t + 1] = u;
+        }
+    }
+    return bad ? -1 : 0;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -87,6 +87,17 @@ struct BcWorkspace {
   }
 };
 
+// Scratch of fg_dfs_batch: per query a stack of (vertex, arc to resume from)
+// and, for a relabelled graph, the discovery ranks in internal order.
+struct DfsWorkspace {
+  DevBuf stack, disc, flag;
+  void release_all() {
+    stack.release();
+    disc.release();
+    flag.release();
+  }
+};
+
 }  // namespace fg
 
 // Graph handle of the C ABI: the partitioned graph on the device, its own
@@ -101,6 +112,7 @@ struct fg_graph {
   fg::DevBuf rp, adj, wt, orig, intl;
   fg::DevBuf deg;                  // out-degree per original id (built by the first fg_ncp_sweep)
   fg::BcWorkspace bc;              // fg_bc_accumulate scratch (guarded by mu)
+  fg::DfsWorkspace dfs;            // fg_dfs_batch scratch (guarded by mu)
   bool has_zero_weight = false;    // some arc has weight 0
   int bc_blocks = 0;               // cooperative grid of the BC kernel (0 = not sized yet)
   size_t graph_bytes = 0;

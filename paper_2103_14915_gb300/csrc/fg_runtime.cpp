@@ -328,6 +328,7 @@ extern "C" fg_status fg_graph_destroy(fg_graph *g) {
     g->rp.release(); g->adj.release(); g->wt.release(); g->orig.release(); g->intl.release();
     g->deg.release();
     g->bc.release_all();
+    g->dfs.release_all();
     if (g->last_done) cudaEventDestroy(g->last_done);
   }
   delete g;

@@ -178,3 +178,6 @@ def test_application_entry_points_reject_bad_arguments_on_the_host(lib):
     st, _ = fg.fg_bc_accumulate(None, src, 1, lab, True, bc)
     assert st == fg.FG_ERR_INVALID_ARG
     assert ctypes.sizeof(fg.fg_bc_info_t) == 16
+    paths = np.zeros(8, dtype=np.int32)
+    assert fg.fg_rw_batch(None, src, 1, 3, 0, paths) == fg.FG_ERR_INVALID_ARG
+    assert fg.fg_dfs_batch(None, src, 1, paths) == fg.FG_ERR_INVALID_ARG
