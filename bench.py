@@ -494,8 +494,8 @@ def run_bc(args):
     import oracle
     from paper_2103_14915_gb300 import fg, inputs
     stream = torch.cuda.current_stream().cuda_stream
-    runs = {"grid": ("grid1024_bfs_sssp", True), "rmat": ("rmat22_ppr", False)}
-    for name, weighted in (runs[k] for k in args.bc_graphs.split(",")):
+    bc_runs = {"grid": ("grid1024_bfs_sssp", True), "rmat": ("rmat22_ppr", False)}
+    for name, weighted in [bc_runs[k] for k in args.bc_graphs.split(",")]:
         g = inputs.workload_graph(name)
         method = fg.FG_PART_GROW if weighted else fg.FG_PART_AUTO
         st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, fg.fg_default_graph_opts(

@@ -187,9 +187,17 @@ __device__ void cut_back(const Stream &st, uint32_t T) {
   for (int shift = 56; shift >= 0; shift -= 8) {
     for (int i = tid; i < 256; i += kThreads) st.h[i] = 0u;
     __syncthreads();
-    for (uint32_t i = tid; i < B; i += kThreads) {
-      const unsigned long long k = st.buf[i];
-      if (shift == 56 || (k >> (shift + 8)) == prefix) atomicAdd(&st.h[(k >> shift) & 255u], 1u);
+    // the leading digits of the held keys fall into few bins: lanes with the
+    // same bin add their count through one atomic (else they serialise)
+    for (uint32_t base = 0; base < B; base += kThreads) {
+      const uint32_t i = base + tid;
+      uint32_t bin = 0xFFFFFFFFu;
+      if (i < B) {
+        const unsigned long long k = st.buf[i];
+        if (shift == 56 || (k >> (shift + 8)) == prefix) bin = (uint32_t)((k >> shift) & 255u);
+      }
+      const unsigned grp = __match_any_sync(0xFFFFFFFFu, bin);
+      if (bin != 0xFFFFFFFFu && lane == __ffs(grp) - 1) atomicAdd(&st.h[bin], (uint32_t)__popc(grp));
     }
     __syncthreads();
     // inclusive prefix over the 256 bins (threads 0..255, warps 0..7)
@@ -236,66 +244,106 @@ __device__ void cut_back(const Stream &st, uint32_t T) {
   __syncthreads();
 }
 
-// Steps 1-2: one pass over the row keeps every vertex whose sort key may still
-// be among the T smallest; the buffer is cut back to T whenever the next tile
-// might not fit. Returns the number held (<= T after the final cut).
-template <bool VEC>
-__device__ uint32_t stream_top(const NcpArgs &a, const float *prow, const Stream &st, uint32_t T) {
+// Admission of one tile (block-wide): each thread offers up to kSlots keys
+// (bit e of `mask` set = key[e] is below the threshold); admitted keys are
+// appended to the buffer, and the barrier that ends the tile decides,
+// uniformly, whether the buffer must be cut before the next tile.
+__device__ __forceinline__ void admit_tile(const Stream &st, uint32_t T, const unsigned long long (&key)[kSlots],
+                                           unsigned mask) {
   const int lane = threadIdx.x & 31;
+  uint32_t held_after = 0;  // lane 0: the count right after this warp's last append
+  if (__any_sync(0xFFFFFFFFu, mask != 0u)) {  // most tiles admit nothing once the buffer is full
+#pragma unroll
+    for (int e = 0; e < kSlots; ++e) {
+      const bool take = (mask >> e) & 1u;
+      const unsigned bal = __ballot_sync(0xFFFFFFFFu, take);
+      if (bal) {
+        uint32_t pos = 0;
+        if (lane == 0) {
+          pos = atomicAdd(st.n_buf, (uint32_t)__popc(bal));
+          held_after = max(held_after, pos + (uint32_t)__popc(bal));
+        }
+        pos = __shfl_sync(0xFFFFFFFFu, pos, 0) + (uint32_t)__popc(bal & ((1u << lane) - 1u));
+        if (take && pos < (uint32_t)kCap) st.buf[pos] = key[e];
+      }
+    }
+  }
+  // The last append of the tile saw the final count. (Reading the count after
+  // a plain barrier would race with the next tile's appends.)
+  if (__syncthreads_or(held_after > (uint32_t)(kCap - kTile))) cut_back(st, T);
+}
+
+__device__ __forceinline__ void stream_begin(const Stream &st) {
   if (threadIdx.x == 0) {
     *st.n_buf = 0u;
     *st.thr = ~0ull;  // every key is admitted until the first cut (real keys are below 2^64 - 2^32)
   }
   __syncthreads();
+}
+
+// The FP32 key value of the threshold (0 while every key is admitted).
+__device__ __forceinline__ float thr_key(unsigned long long thr) {
+  if (thr == ~0ull) return 0.f;
+  const uint32_t enc = ~(uint32_t)(thr >> 32);
+  return __uint_as_float(enc - 1u);
+}
+
+// Steps 1-2 over tiles [tlo, thi) of a row: every vertex whose sort key may
+// still be among the T smallest is kept (the buffer holds at most T after the
+// final cut). Tiles are visited in a scrambled order: step i takes tile
+// tlo + (i * odd) mod P, P = the range rounded up to a power of two (a
+// bijection; steps past the range load nothing), so keys that drift along the
+// vertex ids (degree correlates with id in R-MAT numbering) do not keep
+// beating the threshold.
+//
+// Most vertices end far below the threshold key K, and the exact key needs an
+// IEEE division. A vertex is skipped without it when p < (K (1 - 2^-20)) * d
+// in FP32 (three roundings of at most 2^-24 each: the conversion of d and the
+// two products, so p / d < K (1 - 2^-21) and the rounded key is below K); the
+// test is used only while the products are normal and finite. Every other
+// vertex gets its exact key.
+template <bool VEC>
+__device__ void stream_row(const NcpArgs &a, const float *prow, const Stream &st, uint32_t T, int64_t tlo,
+                           int64_t thi) {
   const int64_t n = a.n;
-  const int64_t ntiles = (n + kTile - 1) / kTile;
-  // Tiles are visited in a scrambled order: step i takes tile (i * odd) mod P,
-  // P = ntiles rounded up to a power of two (a bijection; steps past the row
-  // load nothing). Keys that drift along the vertex ids (degree correlates
-  // with id in R-MAT numbering) would otherwise keep beating the threshold,
-  // and the buffer would be cut every few tiles; in a random order about
-  // top * (1 + ln(#positive / top)) keys are admitted in all.
   int64_t P = 1;
-  while (P < ntiles) P <<= 1;
-  auto tile_at = [P](int64_t i) { return (int64_t)(((uint64_t)i * 0x9E3779B97F4A7C15ull) & (uint64_t)(P - 1)); };
+  while (P < thi - tlo) P <<= 1;
+  auto tile_at = [P, tlo](int64_t i) {
+    return tlo + (int64_t)(((uint64_t)i * 0x9E3779B97F4A7C15ull) & (uint64_t)(P - 1));
+  };
+  const int64_t hi_elem = thi * kTile;  // elements of tiles >= thi belong to another segment
   float pc[kSlots];
   uint32_t dc[kSlots];
-  load_tile<VEC>(prow, a.deg, n, tile_at(0), pc, dc);
+  load_tile<VEC>(prow, a.deg, n, tile_at(0) < thi ? tile_at(0) : (n + kTile) / kTile + 1, pc, dc);
   for (int64_t i = 0; i < P; ++i) {
     const int64_t t = tile_at(i);
     float pn[kSlots] = {};
     uint32_t dn[kSlots] = {};
-    if (i + 1 < P) load_tile<VEC>(prow, a.deg, n, tile_at(i + 1), pn, dn);  // in flight while tile t is filtered
+    if (i + 1 < P) {
+      const int64_t tn = tile_at(i + 1);
+      if (tn < thi) load_tile<VEC>(prow, a.deg, n, tn, pn, dn);  // in flight while tile t is filtered
+    }
     const unsigned long long thr = *st.thr;
+    // Kc = K (1 - 2^-20), rounded; used only while it is a normal number, so
+    // that Kc * d (d >= 1) is normal too (the products stay finite: checked)
+    const float Kc = __fmul_rn(thr_key(thr), 0x1.ffffe0p-1f);
+    const bool filt = Kc >= 1.17549435e-38f;  // FLT_MIN
     unsigned long long key[kSlots];
     unsigned mask = 0;  // slots of this thread that are admitted
 #pragma unroll
     for (int e = 0; e < kSlots; ++e) {
-      const uint32_t enc = key_enc(pc[e], dc[e]);  // 0 past the end of the row (p = 0 there)
-      key[e] = sort_key(enc, (uint32_t)slot_index<VEC>(t, e));
-      if (enc != 0u && key[e] < thr) mask |= 1u << e;
-    }
-    uint32_t held_after = 0;  // lane 0: the count right after this warp's last append
-    if (__any_sync(0xFFFFFFFFu, mask != 0u)) {  // most tiles admit nothing once the buffer is full
-#pragma unroll
-      for (int e = 0; e < kSlots; ++e) {
-        const bool take = (mask >> e) & 1u;
-        const unsigned bal = __ballot_sync(0xFFFFFFFFu, take);
-        if (bal) {
-          uint32_t pos = 0;
-          if (lane == 0) {
-            pos = atomicAdd(st.n_buf, (uint32_t)__popc(bal));
-            held_after = max(held_after, pos + (uint32_t)__popc(bal));
-          }
-          pos = __shfl_sync(0xFFFFFFFFu, pos, 0) + (uint32_t)__popc(bal & ((1u << lane) - 1u));
-          if (take && pos < (uint32_t)kCap) st.buf[pos] = key[e];
-        }
+      const int64_t v = slot_index<VEC>(t, e);
+      key[e] = ~0ull;
+      if (t >= thi || v >= hi_elem || !(pc[e] > 0.f)) continue;
+      if (filt) {
+        const float lim = __fmul_rn(Kc, __uint2float_rn(dc[e] > 0u ? dc[e] : 1u));
+        if (lim <= 3.40282347e+38f && pc[e] < lim) continue;
       }
+      const uint32_t enc = key_enc(pc[e], dc[e]);
+      key[e] = sort_key(enc, (uint32_t)v);
+      if (key[e] < thr) mask |= 1u << e;
     }
-    // The barrier ends the tile and decides, uniformly, whether the next tile
-    // might not fit: the last append of the tile saw the final count. (Reading
-    // the count after a plain barrier would race with the next tile's appends.)
-    if (__syncthreads_or(held_after > (uint32_t)(kCap - kTile))) cut_back(st, T);
+    admit_tile(st, T, key, mask);
 #pragma unroll
     for (int e = 0; e < kSlots; ++e) {
       pc[e] = pn[e];
@@ -303,29 +351,100 @@ __device__ uint32_t stream_top(const NcpArgs &a, const float *prow, const Stream
     }
   }
   if (*st.n_buf > T) cut_back(st, T);
-  return min(*st.n_buf, T);
 }
 
+// Merge: stream `count` keys (segments' survivors, ~0 = padding) through the
+// same buffer; at most T are held afterwards.
+__device__ void stream_keys(const unsigned long long *keys, int64_t count, const Stream &st, uint32_t T) {
+  for (int64_t base = 0; base < count; base += kTile) {
+    const unsigned long long thr = *st.thr;
+    unsigned long long key[kSlots];
+    unsigned mask = 0;
+#pragma unroll
+    for (int e = 0; e < kSlots; ++e) {
+      const int64_t i = base + (int64_t)e * kThreads + threadIdx.x;
+      key[e] = i < count ? __ldcg(keys + i) : ~0ull;
+      if (key[e] < thr) mask |= 1u << e;
+    }
+    admit_tile(st, T, key, mask);
+  }
+  if (*st.n_buf > T) cut_back(st, T);
+}
+
+struct Smem {
+  unsigned long long *cand;
+  uint32_t *hkey, *hval, *ord, *dgs;
+};
+
+__device__ __forceinline__ Smem carve(unsigned char *smem) {
+  Smem m;
+  m.cand = reinterpret_cast<unsigned long long *>(smem);
+  m.hkey = reinterpret_cast<uint32_t *>(smem);
+  m.hval = m.hkey + kHash;
+  m.ord = reinterpret_cast<uint32_t *>(smem + kBytesA);
+  m.dgs = reinterpret_cast<uint32_t *>(smem + kBytesA + kBytesB);
+  return m;
+}
+
+// Steps 2-4 for row q, with the L (<= top) kept keys in cand[0, L).
+__device__ void finish_row(const NcpArgs &a, int64_t q, uint32_t L, const Smem &m);
+
+// One block per row: the whole row streamed, then steps 2-4.
 __global__ void __launch_bounds__(kThreads, 2) ncp_sweep_kernel(NcpArgs a, bool vec) {
   extern __shared__ __align__(16) unsigned char smem[];
-  unsigned long long *cand = reinterpret_cast<unsigned long long *>(smem);
-  uint32_t *hkey = reinterpret_cast<uint32_t *>(smem);
-  uint32_t *hval = hkey + kHash;
-  uint32_t *ord = reinterpret_cast<uint32_t *>(smem + kBytesA);
-  uint32_t *dgs = reinterpret_cast<uint32_t *>(smem + kBytesA + kBytesB);
-  __shared__ unsigned long long s_w64[2][kWarps];
-  __shared__ uint32_t s_h[256], s_w32[kWarps], s_sel[3];
-  __shared__ uint32_t s_n, s_m;
+  const Smem m = carve(smem);
+  __shared__ uint32_t s_h[256], s_w32[kWarps], s_sel[3], s_n, s_m;
   __shared__ unsigned long long s_thr;
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t q = blockIdx.x;
-  const float *prow = a.p + q * a.n;
-  const uint32_t T = (uint32_t)a.top;
+  const Stream st{m.cand, reinterpret_cast<unsigned long long *>(smem + kBytesA), s_h, s_w32, &s_n, &s_m, &s_thr, s_sel};
+  stream_begin(st);
+  const int64_t ntiles = (a.n + kTile - 1) / kTile;
+  if (vec) stream_row<true>(a, a.p + q * a.n, st, (uint32_t)a.top, 0, ntiles);
+  else stream_row<false>(a, a.p + q * a.n, st, (uint32_t)a.top, 0, ntiles);
+  finish_row(a, q, min(*st.n_buf, (uint32_t)a.top), m);
+}
 
-  // ---- 1-2. select and compact in one pass over the row -------------------
-  Stream st{cand, reinterpret_cast<unsigned long long *>(smem + kBytesA), s_h, s_w32, &s_n, &s_m, &s_thr, s_sel};
-  const uint32_t L = vec ? stream_top<true>(a, prow, st, T) : stream_top<false>(a, prow, st, T);
+// `parts` blocks per row: block (q, c) keeps the top keys of segment c of row
+// q and writes them to scratch[(q * parts + c) * top ...], padded with ~0.
+__global__ void __launch_bounds__(kThreads, 2) ncp_select_kernel(NcpArgs a, bool vec, int parts,
+                                                                 unsigned long long *scratch) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Smem m = carve(smem);
+  __shared__ uint32_t s_h[256], s_w32[kWarps], s_sel[3], s_n, s_m;
+  __shared__ unsigned long long s_thr;
+  const int64_t q = blockIdx.x / parts;
+  const int c = (int)(blockIdx.x % parts);
+  const Stream st{m.cand, reinterpret_cast<unsigned long long *>(smem + kBytesA), s_h, s_w32, &s_n, &s_m, &s_thr, s_sel};
+  stream_begin(st);
+  const int64_t ntiles = (a.n + kTile - 1) / kTile;
+  const int64_t tlo = ntiles * c / parts, thi = ntiles * (c + 1) / parts;
+  if (vec) stream_row<true>(a, a.p + q * a.n, st, (uint32_t)a.top, tlo, thi);
+  else stream_row<false>(a, a.p + q * a.n, st, (uint32_t)a.top, tlo, thi);
+  const uint32_t held = min(*st.n_buf, (uint32_t)a.top);
+  unsigned long long *out = scratch + ((size_t)q * parts + c) * (size_t)a.top;
+  for (uint32_t i = threadIdx.x; i < (uint32_t)a.top; i += kThreads) __stcg(out + i, i < held ? m.cand[i] : ~0ull);
+}
+
+// One block per row: merge the row's `parts` segments, then steps 2-4.
+__global__ void __launch_bounds__(kThreads, 2) ncp_merge_kernel(NcpArgs a, int parts,
+                                                                const unsigned long long *scratch) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Smem m = carve(smem);
+  __shared__ uint32_t s_h[256], s_w32[kWarps], s_sel[3], s_n, s_m;
+  __shared__ unsigned long long s_thr;
+  const int64_t q = blockIdx.x;
+  const Stream st{m.cand, reinterpret_cast<unsigned long long *>(smem + kBytesA), s_h, s_w32, &s_n, &s_m, &s_thr, s_sel};
+  stream_begin(st);
+  stream_keys(scratch + (size_t)q * parts * (size_t)a.top, (int64_t)parts * a.top, st, (uint32_t)a.top);
+  finish_row(a, q, min(*st.n_buf, (uint32_t)a.top), m);
+}
+
+__device__ void finish_row(const NcpArgs &a, int64_t q, uint32_t L, const Smem &m) {
+  unsigned long long *cand = m.cand;
+  uint32_t *hkey = m.hkey, *hval = m.hval, *ord = m.ord, *dgs = m.dgs;
+  __shared__ unsigned long long s_w64[2][kWarps];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t T = (uint32_t)a.top;
   const uint32_t kmax = L;
 
   // ---- 2. sort ----------------------------------------------------------
@@ -373,28 +492,89 @@ __global__ void __launch_bounds__(kThreads, 2) ncp_sweep_kernel(NcpArgs a, bool 
     }
   }
   __syncthreads();
-  for (uint32_t k = warp; k < kmax; k += kWarps) {
-    const uint32_t u = ord[k];
-    const uint32_t e0 = __ldg(a.rp + u), e1 = __ldg(a.rp + u + 1);
-    uint32_t inside = 0;
-    for (uint32_t e = e0 + lane; e < e1; e += 32) {
-      const uint32_t w = __ldg(a.adj + e);
-      uint32_t s = (w * 0x9E3779B1u) >> (32 - kHashLog2);
-      for (int probe = 0; probe < kHash; ++probe, s = (s + 1) & (kHash - 1)) {
-        const uint32_t hk = hkey[s];
-        if (hk == w) {
-          inside += hval[s] < k ? 1u : 0u;
-          break;
-        }
-        if (hk == kEmpty) break;
-      }
+  // neighbours ranked before k. The sweep set mixes many light vertices with a
+  // few hubs (tens of thousands of arcs), so the count is split three ways:
+  // a light vertex (<= 32 arcs) is counted by one lane, so that 32 vertices'
+  // load chains are in flight per warp; a medium one by its warp; a hub
+  // (more than kBlockArcs arcs) by the whole block, after the rest. Every
+  // thread keeps 4 arc loads in flight before it probes the hash.
+  constexpr uint32_t kBlockArcs = 4096;
+  constexpr int kMaxHubs = 64;
+  __shared__ uint32_t s_hub[kMaxHubs], s_nhub, s_red[kWarps];
+  auto ranked_before = [&](uint32_t w, uint32_t k) -> uint32_t {
+    uint32_t sl = (w * 0x9E3779B1u) >> (32 - kHashLog2);
+    for (int probe = 0; probe < kHash; ++probe, sl = (sl + 1) & (kHash - 1)) {
+      const uint32_t hk = hkey[sl];
+      if (hk == w) return hval[sl] < k ? 1u : 0u;
+      if (hk == kEmpty) return 0u;
     }
+    return 0u;
+  };
+  // arcs [b, e1) with stride `step`, 4 loads in flight per thread
+  auto count_arcs = [&](uint32_t b, uint32_t e1, uint32_t step, uint32_t k) -> uint32_t {
+    uint32_t inside = 0;
+    for (uint32_t e = b; e < e1; e += 4 * step) {
+      uint32_t w4[4];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) inside += __shfl_xor_sync(0xFFFFFFFFu, inside, o);
-    __syncwarp();
-    if (lane == 0) ord[k] = (uint32_t)((int32_t)dgs[k] - 2 * (int32_t)inside);
+      for (int j = 0; j < 4; ++j) w4[j] = e + j * step < e1 ? __ldg(a.adj + e + j * step) : kEmpty;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (w4[j] != kEmpty) inside += ranked_before(w4[j], k);
+    }
+    return inside;
+  };
+  if (tid == 0) s_nhub = 0;
+  __syncthreads();
+  for (uint32_t k0 = warp * 32; k0 < kmax; k0 += kWarps * 32) {
+    const uint32_t k = k0 + lane;
+    uint32_t e0 = 0, e1 = 0;
+    if (k < kmax) {
+      const uint32_t u = ord[k];
+      e0 = __ldg(a.rp + u);
+      e1 = __ldg(a.rp + u + 1);
+    }
+    const bool light = k < kmax && e1 - e0 <= 32u;
+    if (light) ord[k] = (uint32_t)((int32_t)dgs[k] - 2 * (int32_t)count_arcs(e0, e1, 1u, k));
+    unsigned heavy = __ballot_sync(0xFFFFFFFFu, k < kmax && !light);
+    while (heavy) {
+      const int j = __ffs(heavy) - 1;
+      heavy &= heavy - 1;
+      const uint32_t kh = k0 + j;
+      const uint32_t h0 = __shfl_sync(0xFFFFFFFFu, e0, j), h1 = __shfl_sync(0xFFFFFFFFu, e1, j);
+      if (h1 - h0 > kBlockArcs) {
+        uint32_t slot = 0;
+        if (lane == 0) slot = atomicAdd(&s_nhub, 1u);
+        slot = __shfl_sync(0xFFFFFFFFu, slot, 0);
+        if (slot < (uint32_t)kMaxHubs) {
+          if (lane == 0) s_hub[slot] = kh;  // counted by the block below
+          continue;
+        }
+      }
+      uint32_t inside = count_arcs(h0 + lane, h1, 32u, kh);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) inside += __shfl_xor_sync(0xFFFFFFFFu, inside, o);
+      if (lane == j) ord[kh] = (uint32_t)((int32_t)dgs[kh] - 2 * (int32_t)inside);
+    }
   }
   __syncthreads();
+  const uint32_t nhub = min(s_nhub, (uint32_t)kMaxHubs);
+  for (uint32_t i = 0; i < nhub; ++i) {
+    const uint32_t kh = s_hub[i];
+    // ord[kh] still holds the hub's internal id: every thread reads it before the write below
+    const uint32_t u = ord[kh];
+    const uint32_t h0 = __ldg(a.rp + u), h1 = __ldg(a.rp + u + 1);
+    uint32_t inside = count_arcs(h0 + tid, h1, kThreads, kh);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) inside += __shfl_xor_sync(0xFFFFFFFFu, inside, o);
+    if (lane == 0) s_red[warp] = inside;
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t tot = 0;
+      for (int w = 0; w < kWarps; ++w) tot += s_red[w];
+      ord[kh] = (uint32_t)((int32_t)dgs[kh] - 2 * (int32_t)tot);
+    }
+    __syncthreads();
+  }
 
   // ---- 4. scan ----------------------------------------------------------
   const uint32_t per = (kmax + kThreads - 1) / kThreads;
@@ -489,6 +669,10 @@ extern "C" fg_status fg_ncp_sweep(fg_graph *g, const float *p, int32_t nq, int32
       static cudaError_t attr_err = cudaSuccess;
       std::call_once(attr_once, [] {
         attr_err = cudaFuncSetAttribute(ncp_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+        if (attr_err == cudaSuccess)
+          attr_err = cudaFuncSetAttribute(ncp_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+        if (attr_err == cudaSuccess)
+          attr_err = cudaFuncSetAttribute(ncp_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
       });
       CUDA_TRY(attr_err);
       DevBuf d;
@@ -523,8 +707,30 @@ extern "C" fg_status fg_ncp_sweep(fg_graph *g, const float *p, int32_t nq, int32
     CUDA_TRY(cudaGetLastError());
   }
   const bool vec = (n % 4 == 0) && aligned(p, 16);
-  ncp_sweep_kernel<<<nq, kThreads, kSmem, stream>>>(a, vec);
-  CUDA_TRY(cudaGetLastError());
+  // Rows are split into `parts` segments when there are too few rows to give
+  // every SM two blocks: each segment's block keeps its top keys, and one
+  // block per row merges them (the kept set does not depend on the split).
+  int sms = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  int64_t parts = (4ll * sms + nq - 1) / nq;
+  parts = std::min<int64_t>(std::min<int64_t>(parts, 16), ntiles / 4);
+  if (parts <= 1) {
+    ncp_sweep_kernel<<<nq, kThreads, kSmem, stream>>>(a, vec);
+    CUDA_TRY(cudaGetLastError());
+  } else {
+    unsigned long long *scratch = nullptr;
+    const size_t bytes = (size_t)nq * (size_t)parts * (size_t)top * sizeof(unsigned long long);
+    CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&scratch), bytes, stream));
+    ncp_select_kernel<<<(unsigned)(nq * parts), kThreads, kSmem, stream>>>(a, vec, (int)parts, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+      ncp_merge_kernel<<<nq, kThreads, kSmem, stream>>>(a, (int)parts, scratch);
+      e = cudaGetLastError();
+    }
+    cudaFreeAsync(scratch, stream);
+    CUDA_TRY(e);
+  }
   if (a.ncp) {
     ncp_profile_end<<<(top + 255) / 256, 256, 0, stream>>>(a.ncp, top);
     CUDA_TRY(cudaGetLastError());

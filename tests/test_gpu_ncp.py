@@ -154,6 +154,52 @@ def test_sparse_zero_and_odd_rows():
         fg.fg_graph_destroy(h)
 
 
+def test_rows_split_across_blocks():
+    # few rows on a larger graph: each row is split into segments whose survivors are merged
+    g = inputs.rmat(16, 8, seed=51)
+    h = _graph(g, fg.FG_PART_GROW, 0)
+    try:
+        rows = _ppr_rows(g, inputs.sources_uniform(g, 8, seed=52), eps=1e-6)
+        c = _check(g, h, rows, fg.FG_NCP_MAX_TOP)
+        assert c.min() > 1000
+        _check(g, h, rows[:1], 777)
+    finally:
+        fg.fg_graph_destroy(h)
+    g = inputs.grid(200, 200, 0, 0, seed=53)  # exact ties across segment boundaries
+    h = _graph(g, fg.FG_PART_GROW, 512)
+    try:
+        rows = np.ones((2, g.n), dtype=np.float32)
+        rows[1, 10000:] = 0.25
+        _check(g, h, rows, fg.FG_NCP_MAX_TOP)
+    finally:
+        fg.fg_graph_destroy(h)
+
+
+def test_hubs_in_the_sweep_set():
+    # a star whose centre (9,000 arcs) is swept first: counted by the whole block
+    n = 9001
+    g = inputs.from_edges(n, [(0, i) for i in range(1, n)])
+    h = _graph(g, fg.FG_PART_RANGE, 0)
+    try:
+        rows = np.full((2, n), 1e-3, dtype=np.float32)
+        rows[:, 0] = 50.0
+        rows[1, 1::2] = 2e-3
+        _check(g, h, rows, fg.FG_NCP_MAX_TOP)
+    finally:
+        fg.fg_graph_destroy(h)
+    # K(70, 5000): 70 hubs of 5,000 arcs in the set, more than the block queue holds
+    hubs, leaves = 70, 5000
+    g = inputs.from_edges(hubs + leaves, [(i, hubs + j) for i in range(hubs) for j in range(leaves)])
+    h = _graph(g, fg.FG_PART_GROW, 512)
+    try:
+        rng = np.random.default_rng(54)
+        rows = rng.random((2, g.n)).astype(np.float32) * np.float32(1e-3)
+        rows[:, :hubs] += np.float32(1e4)
+        _check(g, h, rows, fg.FG_NCP_MAX_TOP)
+    finally:
+        fg.fg_graph_destroy(h)
+
+
 def test_profile_accumulates_over_calls():
     g = inputs.grid(40, 40, 100, 20, seed=48)
     h = _graph(g)
