@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--bc-graphs", default="grid,rmat", help="BC runs to do: grid (SSSP), rmat (BFS)")
     ap.add_argument("--walks", action="store_true",
                     help="only the query types without a batch engine form: random walks and DFS")
+    ap.add_argument("--local-ppr", action="store_true",
+                    help="only local PPR: sparse per-query state against the dense batch on R-MAT s22, eps 1e-4")
     ap.add_argument("--ll", action="store_true",
                     help="only the LL application: 1,024 SSSPs on the grid, labels, 2^20 distance queries")
     ap.add_argument("--ll-pairs", type=int, default=1 << 20, help="pairs per query batch of the LL run")
@@ -632,6 +634,77 @@ def run_walks(args):
     fg.fg_graph_destroy(h)
 
 
+def run_local_ppr(args):
+    """Local PPR on R-MAT s22 (the 4,096 log-degree seeds, alpha 0.15, eps 1e-4):
+    sparse per-query state (fg_ppr_local_batch, tables of 2^17 slots) against the
+    dense batch (fg_ppr_batch) at the same eps. One JSON line with both rates,
+    the scratch each needs, the mass error, and sampled rows against the
+    oracle's FP64 push at eps / 100 (bound eps * d + eps / 100 * d + 1e-6)."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda:0")
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    from paper_2103_14915_gb300 import fg, inputs
+    alpha, eps, cap = 0.15, 1e-4, 1 << 17
+    g = inputs.workload_graph("rmat22_ppr")
+    st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, fg.fg_default_graph_opts())
+    fg.check(st)
+    srcs = inputs.workload_sources("rmat22_ppr", g)
+    nq = len(srcs)
+    s_d = torch.from_numpy(srcs).to(dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    vert = torch.empty((nq, cap), dtype=torch.int32, device=dev)
+    pl = torch.empty((nq, cap), dtype=torch.float32, device=dev)
+    cnt = torch.empty(nq, dtype=torch.int32, device=dev)
+    mass = torch.empty(nq, dtype=torch.float64, device=dev)
+
+    def timed(fn, reps=3):
+        out = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        return sorted(out)[len(out) // 2]
+
+    local = lambda: fg.check(fg.fg_ppr_local_batch(h, s_d, nq, alpha, eps, cap, vert, pl, cnt, mass, stream))
+    local()
+    t_local = timed(local)
+    c = cnt.cpu().numpy()
+    m_err = float((mass - 1.0).abs().max())
+    rows = [0, nq // 2, nq - 1]
+    deg = np.maximum(np.diff(g.row_ptr), 1).astype(np.float64)
+    ok = True
+    for q in rows:
+        ref = oracle.ppr_push(g, int(srcs[q]), alpha, eps / 100)[0]
+        got = np.zeros(g.n)
+        k = int(c[q])
+        if k >= 0:
+            got[vert[q, :k].cpu().numpy()] = pl[q, :k].cpu().numpy()
+            ok &= bool(np.all(np.abs(got - ref) <= eps * deg * 1.01 + 1e-6))
+    del vert, pl
+    # the dense batch at the same eps (the library splits the batch to fit HBM)
+    pd = torch.empty((256, g.n), dtype=torch.float32, device=dev)
+    dense = lambda: fg.check(fg.fg_ppr_batch(h, s_d[:256], 256, alpha, eps, pd, None, None, stream, None))
+    dense()
+    fg.check(fg.fg_sync(stream))
+    t_dense = timed(dense)
+    print(json.dumps({
+        "metric": "local PPR", "workload": "rmat22_ppr_local", "n": g.n, "m": g.m, "seeds": nq, "alpha": alpha,
+        "eps": eps, "data": "synthetic", "sparse_ms": t_local, "sparse_qps": nq / (t_local / 1e3),
+        "sparse_scratch_bytes": 24 * nq * cap, "table_slots": cap, "tables_full": int((c < 0).sum()),
+        "support_median": int(np.median(c[c >= 0])) if (c >= 0).any() else None,
+        "mass_err_max": m_err, "bound_ok_sampled": ok,
+        "dense_qps": 256 / (t_dense / 1e3), "dense_bytes_per_query": 12 * g.n,
+        "dense_sample": 256}), flush=True)
+    fg.fg_graph_destroy(h)
+
+
 def run_ll(args):
     """LL application (Sec. 1, 6.1): 1,024 SSSPs from random landmarks on the grid
     workload, label construction (query-major rows to vertex-major labels) and a
@@ -865,6 +938,9 @@ def main():
         return
     if args.walks:
         run_walks(args)
+        return
+    if args.local_ppr:
+        run_local_ppr(args)
         return
     if args.configs:
         run_configs(args)

@@ -459,6 +459,29 @@ fg_status fg_rw_batch(const fg_graph *g, const int32_t *src, int32_t nq, int32_t
  */
 fg_status fg_dfs_batch(fg_graph *g, const int32_t *src, int32_t nq, uint32_t *disc_out, void *stream);
 
+/*
+ * Personalized PageRank with sparse per-query state, for local queries: the
+ * push rule of fg_ppr_batch (same alpha, eps, dangling and compensation
+ * rules; synchronous rounds), but each query keeps only the vertices it
+ * touches, in an open-addressing table of `cap` slots (a power of two in
+ * [64, 2^24]), so a batch needs about 24 * nq * cap bytes of scratch (from
+ * the stream-ordered allocator) instead of 12 * nq * n.
+ *
+ * Outputs (DEVICE pointers owned by the caller): vert_out int32[nq * cap] and
+ * p_out float[nq * cap] hold, in the first count_out[q] entries of row q, the
+ * vertices with p(v) > 0 (original ids, in no particular order) and their
+ * estimates; every other vertex has p(v) = 0. count_out[q] = -1 when the
+ * query touched more than 3/4 of `cap` vertices (its row is then not valid:
+ * retry with a larger cap or use fg_ppr_batch). mass_out double[nq]
+ * (nullable) = sum(p) + sum(r) of the query in FP64.
+ *
+ * Requires 0 < alpha < 1 and eps > 0. Synchronous: enqueues on `stream`,
+ * waits, returns FG_ERR_INVALID_ARG for a source id outside [0, n) (that
+ * query's count is 0).
+ */
+fg_status fg_ppr_local_batch(const fg_graph *g, const int32_t *src, int32_t nq, float alpha, float eps, int32_t cap,
+                             int32_t *vert_out, float *p_out, int32_t *count_out, double *mass_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,7 +96,7 @@ EXPORTS = ("fg_default_opts", "fg_default_graph_opts", "fg_graph_create", "fg_gr
            "fg_last_error", "fg_stats", "fg_partition_plan", "fg_sssp_batch_noalloc", "fg_default_server_opts",
            "fg_server_create", "fg_server_destroy", "fg_server_submit", "fg_server_poll", "fg_server_info",
            "fg_server_release", "fg_tune_opts", "fg_ncp_sweep", "fg_ll_build_labels", "fg_ll_query",
-           "fg_bc_accumulate", "fg_rw_batch", "fg_dfs_batch")
+           "fg_bc_accumulate", "fg_rw_batch", "fg_dfs_batch", "fg_ppr_local_batch")
 
 FG_NOALLOC_MAX_VERTICES = 1 << 20
 FG_NCP_MAX_TOP = 4096
@@ -138,6 +138,7 @@ def load():
     lib.fg_bc_accumulate.argtypes = [vp, vp, i32, vp, i32, vp, i32, ctypes.POINTER(fg_bc_info_t), vp]
     lib.fg_rw_batch.argtypes = [vp, vp, i32, i32, ctypes.c_uint64, vp, vp]
     lib.fg_dfs_batch.argtypes = [vp, vp, i32, vp, vp]
+    lib.fg_ppr_local_batch.argtypes = [vp, vp, i32, f32, f32, i32, vp, vp, vp, vp, vp]
     lib.fg_tune_opts.argtypes = [vp, i32, vp, i32, vp, ctypes.POINTER(fg_opts), ctypes.POINTER(fg_tune_report)]
     u64p = ctypes.POINTER(ctypes.c_uint64)
     lib.fg_default_server_opts.argtypes = [ctypes.POINTER(fg_server_opts)]
@@ -305,6 +306,12 @@ def fg_rw_batch(g, src, nq, length, seed, paths_out, stream=None) -> int:
 def fg_dfs_batch(g, src, nq, disc_out, stream=None) -> int:
     """DFS discovery ranks into disc_out (device uint32 / int32[nq, n]); synchronous."""
     return load().fg_dfs_batch(g, _ptr(src), nq, _ptr(disc_out), _stream(stream))
+
+
+def fg_ppr_local_batch(g, src, nq, alpha, eps, cap, vert_out, p_out, count_out, mass_out=None, stream=None) -> int:
+    """Local PPR with sparse state: per query the support (vertex, estimate) in rows of cap entries; synchronous."""
+    return load().fg_ppr_local_batch(g, _ptr(src), nq, alpha, eps, cap, _ptr(vert_out), _ptr(p_out), _ptr(count_out),
+                                     _ptr(mass_out), _stream(stream))
 
 
 def fg_default_server_opts(**overrides) -> fg_server_opts:

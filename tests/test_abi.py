@@ -181,3 +181,5 @@ def test_application_entry_points_reject_bad_arguments_on_the_host(lib):
     paths = np.zeros(8, dtype=np.int32)
     assert fg.fg_rw_batch(None, src, 1, 3, 0, paths) == fg.FG_ERR_INVALID_ARG
     assert fg.fg_dfs_batch(None, src, 1, paths) == fg.FG_ERR_INVALID_ARG
+    pf = np.zeros(64, dtype=np.float32)
+    assert fg.fg_ppr_local_batch(None, src, 1, 0.15, 1e-4, 64, paths, pf, cnt) == fg.FG_ERR_INVALID_ARG
