@@ -11,7 +11,8 @@
 //   label construction  [K][n] -> [n][K] transpose through 64 x 64 shared-memory
 //                       tiles (each warp reads and writes 256 contiguous bytes
 //                       per row; the padded tile keeps both phases free of bank
-//                       conflicts); 8 * K * n bytes;
+//                       conflicts), persistent blocks that load the next tile
+//                       while writing the current one; 8 * K * n bytes;
 //   query               one warp per pair reads the two K-entry labels with
 //                       16-byte loads (K a multiple of 4) and reduces the
 //                       minimum with shuffles; 8 * K + 16 bytes per pair.
@@ -27,29 +28,49 @@ constexpr int kT = 64;          // transpose tile
 constexpr int kTRows = 8;       // thread rows per tile (block 32 x 8)
 constexpr int kQThreads = 256;  // query block: 8 warps, one pair per warp at a time
 
+// Persistent over tiles: block b takes tiles b, b + gridDim.x, ... (vertex
+// tiles fastest, so neighbouring blocks read neighbouring row segments). Each
+// thread holds its 16 elements of the next tile in registers, loaded while
+// the current tile is written out of shared memory.
 __global__ void __launch_bounds__(32 * kTRows) ll_transpose(const uint32_t *__restrict__ dist, int32_t K, int64_t n,
-                                                            uint32_t *__restrict__ labels) {
+                                                            uint32_t *__restrict__ labels, int64_t ntv, int64_t ntiles) {
   __shared__ uint32_t tile[kT][kT + 1];
-  const int64_t v0 = (int64_t)blockIdx.x * kT;
-  const int32_t k0 = (int32_t)blockIdx.y * kT;
   const int tx = threadIdx.x, ty = threadIdx.y;
+  constexpr int kPer = (kT / kTRows) * (kT / 32);  // elements per thread per tile
+  uint32_t buf[kPer];
+  auto load = [&](int64_t t) {
+    const int64_t v0 = (t % ntv) * kT;
+    const int64_t k0 = (t / ntv) * kT;
 #pragma unroll
-  for (int r = ty; r < kT; r += kTRows) {
-    const int32_t k = k0 + r;
+    for (int r = 0; r < kT / kTRows; ++r) {
+      const int64_t k = k0 + ty + r * kTRows;
 #pragma unroll
-    for (int c = tx; c < kT; c += 32) {
-      const int64_t v = v0 + c;
-      if (k < K && v < n) tile[r][c] = __ldcs(dist + (size_t)k * (size_t)n + (size_t)v);
+      for (int c = 0; c < kT / 32; ++c) {
+        const int64_t v = v0 + tx + c * 32;
+        buf[r * (kT / 32) + c] = (k < K && v < n) ? __ldcs(dist + (size_t)k * (size_t)n + (size_t)v) : 0u;
+      }
     }
-  }
-  __syncthreads();
+  };
+  int64_t t = blockIdx.x;
+  if (t < ntiles) load(t);
+  for (; t < ntiles; t += gridDim.x) {
+    __syncthreads();  // the previous tile has been written out of shared memory
 #pragma unroll
-  for (int r = ty; r < kT; r += kTRows) {
-    const int64_t v = v0 + r;
+    for (int r = 0; r < kT / kTRows; ++r)
 #pragma unroll
-    for (int c = tx; c < kT; c += 32) {
-      const int32_t k = k0 + c;
-      if (k < K && v < n) __stcs(labels + (size_t)v * (size_t)K + (size_t)k, tile[c][r]);
+      for (int c = 0; c < kT / 32; ++c) tile[ty + r * kTRows][tx + c * 32] = buf[r * (kT / 32) + c];
+    __syncthreads();
+    const int64_t v0 = (t % ntv) * kT;
+    const int64_t k0 = (t / ntv) * kT;
+    if (t + gridDim.x < ntiles) load(t + gridDim.x);  // in flight during the write-out below
+#pragma unroll
+    for (int r = 0; r < kT / kTRows; ++r) {
+      const int64_t v = v0 + ty + r * kTRows;
+#pragma unroll
+      for (int c = 0; c < kT / 32; ++c) {
+        const int64_t k = k0 + tx + c * 32;
+        if (k < K && v < n) __stcs(labels + (size_t)v * (size_t)K + (size_t)k, tile[tx + c * 32][ty + r * kTRows]);
+      }
     }
   }
 }
@@ -105,12 +126,16 @@ extern "C" fg_status fg_ll_build_labels(const uint32_t *dist, int32_t K, int64_t
                                         void *stream_v) {
   if (!dist || !labels) return fail(FG_ERR_INVALID_ARG, "dist or labels is NULL");
   if (K < 1 || n < 1) return fail(FG_ERR_INVALID_ARG, "K and n must be >= 1 (got %d, %lld)", K, (long long)n);
-  if ((n + kT - 1) / kT > 0x7FFFFFFFll || (K + kT - 1) / kT > 65535)
-    return fail(FG_ERR_UNSUPPORTED, "label matrix too large for one launch");
   if (!aligned(dist, 4) || !aligned(labels, 4)) return fail(FG_ERR_INVALID_ARG, "misaligned pointer");
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_v);
-  const dim3 grid((unsigned)((n + kT - 1) / kT), (unsigned)((K + kT - 1) / kT));
-  ll_transpose<<<grid, dim3(32, kTRows), 0, stream>>>(dist, K, n, labels);
+  int dev = 0, sms = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t ntv = (n + kT - 1) / kT, ntk = ((int64_t)K + kT - 1) / kT, ntiles = ntv * ntk;
+  int per_sm = 0;
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ll_transpose, 32 * kTRows, 0));
+  const int64_t blocks = std::min<int64_t>(ntiles, (int64_t)sms * std::max(per_sm, 1));  // all resident
+  ll_transpose<<<(unsigned)blocks, dim3(32, kTRows), 0, stream>>>(dist, K, n, labels, ntv, ntiles);
   CUDA_TRY(cudaGetLastError());
   return FG_OK;
 }

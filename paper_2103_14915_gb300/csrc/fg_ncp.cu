@@ -92,17 +92,6 @@ __device__ __forceinline__ double dbl_dec(unsigned long long e) {
   return __longlong_as_double((long long)b);
 }
 
-// Inclusive suffix sum within a warp (lane i gets the sum over lanes >= i).
-template <typename T>
-__device__ __forceinline__ T warp_suffix_incl(T x, int lane) {
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const T y = __shfl_down_sync(0xFFFFFFFFu, x, o);
-    if (lane + o < 32) x += y;
-  }
-  return x;
-}
-
 // Inclusive prefix sum within a warp.
 template <typename T>
 __device__ __forceinline__ T warp_prefix_incl(T x, int lane) {
@@ -171,7 +160,7 @@ struct Stream {
   uint32_t *n_buf;          // candidates held
   uint32_t *n_tmp;
   unsigned long long *thr;  // keys >= thr cannot rank among the top any more
-  uint32_t *sel;            // [3] bucket, keys below it, keys in it
+  uint32_t *sel;            // [2] bucket of the top-th key, keys below that bucket
 };
 
 // Cut the buffer back to its T smallest keys (block-wide; B = held > T).
@@ -393,7 +382,7 @@ __device__ void finish_row(const NcpArgs &a, int64_t q, uint32_t L, const Smem &
 __global__ void __launch_bounds__(kThreads, 2) ncp_sweep_kernel(NcpArgs a, bool vec) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Smem m = carve(smem);
-  __shared__ uint32_t s_h[256], s_w32[kWarps], s_sel[3], s_n, s_m;
+  __shared__ uint32_t s_h[256], s_w32[kWarps], s_sel[2], s_n, s_m;
   __shared__ unsigned long long s_thr;
   const int64_t q = blockIdx.x;
   const Stream st{m.cand, reinterpret_cast<unsigned long long *>(smem + kBytesA), s_h, s_w32, &s_n, &s_m, &s_thr, s_sel};
@@ -410,7 +399,7 @@ __global__ void __launch_bounds__(kThreads, 2) ncp_select_kernel(NcpArgs a, bool
                                                                  unsigned long long *scratch) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Smem m = carve(smem);
-  __shared__ uint32_t s_h[256], s_w32[kWarps], s_sel[3], s_n, s_m;
+  __shared__ uint32_t s_h[256], s_w32[kWarps], s_sel[2], s_n, s_m;
   __shared__ unsigned long long s_thr;
   const int64_t q = blockIdx.x / parts;
   const int c = (int)(blockIdx.x % parts);
@@ -430,7 +419,7 @@ __global__ void __launch_bounds__(kThreads, 2) ncp_merge_kernel(NcpArgs a, int p
                                                                 const unsigned long long *scratch) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Smem m = carve(smem);
-  __shared__ uint32_t s_h[256], s_w32[kWarps], s_sel[3], s_n, s_m;
+  __shared__ uint32_t s_h[256], s_w32[kWarps], s_sel[2], s_n, s_m;
   __shared__ unsigned long long s_thr;
   const int64_t q = blockIdx.x;
   const Stream st{m.cand, reinterpret_cast<unsigned long long *>(smem + kBytesA), s_h, s_w32, &s_n, &s_m, &s_thr, s_sel};
