@@ -1,5 +1,5 @@
-"""The applications' hand-worked fixtures (tests/golden/apps_hand.txt, with
-their derivations) against the oracle on the CPU and the CUDA path on the GPU."""
+"""The applications' and DFS's hand-worked fixtures (tests/golden/apps_hand.txt,
+with their derivations) against the oracle on the CPU and the CUDA path on the GPU."""
 from fractions import Fraction
 from pathlib import Path
 
@@ -13,7 +13,7 @@ FIX = Path(__file__).parent / "golden" / "apps_hand.txt"
 
 
 def _fixture():
-    bc, ll, ncp = [], [], {}
+    bc, ll, ncp, dfs = [], [], {}, []
     for line in FIX.read_text().splitlines():
         if not line or line.startswith("#"):
             continue
@@ -27,7 +27,9 @@ def _fixture():
             ncp["order"] = [int(x) for x in f[2:]]
         elif f[0] == "ncp" and f[1] == "phi":
             ncp["phi"] = [float(Fraction(x)) for x in f[2:]]
-    return bc, ll, ncp
+        elif f[0] == "dfs":
+            dfs.append((int(f[1]), [int(x) for x in f[2:]]))
+    return bc, ll, ncp, dfs
 
 
 def _g_bc():
@@ -42,7 +44,7 @@ P_NCP = np.array([0.5, 0.25, 0.375, 0.0625, 0.0, 0.03125], dtype=np.float32)
 
 
 def test_oracle_bc_matches_the_hand_values():
-    bc, _, _ = _fixture()
+    bc, _, _, _ = _fixture()
     g = _g_bc()
     for weighted, srcs, exp in bc:
         got, _, exact = oracle.bc(g, srcs, weighted)
@@ -50,17 +52,23 @@ def test_oracle_bc_matches_the_hand_values():
 
 
 def test_oracle_ll_matches_the_hand_values():
-    _, ll, _ = _fixture()
+    _, ll, _, _ = _fixture()
     lab = oracle.ll_labels(oracle.sssp(_g_bc(), [0, 3]))
     pairs = np.array([(u, v) for u, v, _ in ll], dtype=np.int32)
     assert oracle.ll_query(lab, pairs).tolist() == [e for _, _, e in ll]
 
 
 def test_oracle_ncp_matches_the_hand_values():
-    _, _, ncp = _fixture()
+    _, _, ncp, _ = _fixture()
     order, phi, count = oracle.ncp_sweep(_g_ncp(), P_NCP[None, :], 6)
     assert count[0] == 5 and order[0, :5].tolist() == ncp["order"]
     assert np.array_equal(phi[0, :5], np.array(ncp["phi"]))
+
+
+def test_oracle_dfs_matches_the_hand_values():
+    _, _, _, dfs = _fixture()
+    for s, exp in dfs:
+        assert oracle.dfs(_g_bc(), [s])[0].tolist() == exp
 
 
 @pytest.mark.gpu
@@ -70,7 +78,7 @@ def test_cuda_path_matches_the_hand_values():
     build.build()
     fg.load()
     dev = "cuda:0"
-    bc, ll, ncp = _fixture()
+    bc, ll, ncp, dfs = _fixture()
     g = _g_bc()
     st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, fg.fg_default_graph_opts())
     fg.check(st)
@@ -94,6 +102,11 @@ def test_cuda_path_matches_the_hand_values():
         fg.check(fg.fg_ll_query(lab, g.n, 2, pairs, len(ll), est))
         fg.check(fg.fg_sync())
         assert est.cpu().tolist() == [e for _, _, e in ll]
+        for src, exp in dfs:
+            s1 = torch.tensor([src], dtype=torch.int32, device=dev)
+            disc = torch.empty((1, g.n), dtype=torch.int32, device=dev)
+            fg.check(fg.fg_dfs_batch(h, s1, 1, disc))
+            assert disc[0].cpu().tolist() == exp
     finally:
         fg.fg_graph_destroy(h)
     g = _g_ncp()
