@@ -22,6 +22,7 @@
 // The waves of all sources advance together, separated by device-wide
 // barriers (bounded waits); their number is the longest hop count of any
 // source's shortest-path DAG.
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -33,6 +34,7 @@ namespace fg {
 namespace {
 
 constexpr int kBcThreads = 256;
+constexpr uint32_t kRoadDegree = 64;  // max out-degree up to which a graph takes one block per source
 constexpr double kExactLimit = 9007199254740992.0;  // 2^53
 
 // Counters of one launch (zeroed before it). Wave t appends the vertices it
@@ -309,6 +311,142 @@ __global__ void __launch_bounds__(kBcThreads) bc_kernel(BcArgs a) {
   }
 }
 
+// ---- one block per source ---------------------------------------------------
+// Road-like graphs (small out-degrees) have deep shortest-path DAGs: the grid
+// workload needs about 2,000 waves, each holding only a wavefront of every
+// source. There one block runs one source: the waves of a source are
+// separated by the block's own barrier instead of a device-wide one, and
+// different sources advance independently. The gather over the sources runs
+// afterwards as its own launch (bc_gather_kernel). Same operations, same
+// order, same results as bc_kernel.
+constexpr int kBcBlockThreads = 1024;
+
+__global__ void __launch_bounds__(kBcBlockThreads) bc_block_kernel(BcArgs a) {
+  const int64_t n = a.g.n;
+  const int64_t q = blockIdx.x;
+  const int64_t row = q * n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // per-source wave list (n entries) and wave starts (a source has at most n
+  // waves, so n + 2 entries), carved from the (query, vertex) buffer read as
+  // 32-bit words: it holds 2 * nq * n + 2 * nq of them
+  uint32_t *wl = reinterpret_cast<uint32_t *>(a.wave) + row;
+  uint32_t *wo = reinterpret_cast<uint32_t *>(a.wave) + (int64_t)a.nq * n + q * (n + 2);
+  __shared__ uint32_t s_cnt[3];
+  __shared__ int s_bad;
+  __shared__ double s_red[kBcBlockThreads / 32];
+
+  for (int64_t i = tid; i < n; i += kBcBlockThreads) {
+    a.pc[row + i] = 0u;
+    a.sigma[row + i] = 0.0;
+    a.delta[row + i] = 0.0;
+    if (a.dint) a.dint[row + i] = __ldg(a.dist + row + __ldg(a.g.orig + i));
+  }
+  const int32_t s = a.src[q];
+  if (tid == 0) {
+    s_bad = (s < 0 || (int64_t)s >= n || __ldg(a.dist + row + s) != 0u) ? 1 : 0;
+    if (s_bad) raise_status(a.ctrl, FG_ERR_INVALID_ARG, kSiteSource);
+    s_cnt[0] = s_cnt[1] = s_cnt[2] = 0u;
+  }
+  __syncthreads();
+  if (s_bad) return;
+  const uint32_t s_int = a.g.intl ? (uint32_t)a.g.intl[s] : (uint32_t)s;
+  if (tid == 0) {
+    a.sigma[row + s_int] = 1.0;
+    wl[0] = s_int;
+    wo[0] = 0u;
+    wo[1] = 1u;
+  }
+  // count tight in-arcs
+  for (int64_t u = tid; u < n; u += kBcBlockThreads) {
+    const uint32_t du = dist_of(a, q, (uint32_t)u);
+    if (du == kInf) continue;
+    const uint32_t e0 = __ldg(a.g.rp + u), e1 = __ldg(a.g.rp + u + 1);
+    for (uint32_t e = e0; e < e1; ++e) {
+      const uint32_t w = __ldg(a.g.adj + e);
+      const uint32_t wt = a.weighted ? __ldg(a.g.wt + e) : 1u;
+      if (tight(du, wt, dist_of(a, q, w))) atomicAdd(a.pc + row + w, 1u);
+    }
+  }
+  __syncthreads();
+  // forward waves; wave t appends through s_cnt[(t + 1) % 3], and the counter
+  // of wave t + 1 is cleared during wave t (its last reader passed a barrier)
+  double smax = 0.0;
+  uint32_t beg = 0, end = 1, waves = 0;
+  while (end > beg) {
+    if (tid == 0) s_cnt[(waves + 2) % 3] = 0u;
+    for (uint32_t i = beg + tid; i < end; i += kBcBlockThreads) {
+      const uint32_t u = __ldcg(wl + i);
+      const double su = __ldcg(a.sigma + row + u);
+      const uint32_t du = dist_of(a, q, u);
+      const uint32_t e0 = __ldg(a.g.rp + u), e1 = __ldg(a.g.rp + u + 1);
+      for (uint32_t e = e0; e < e1; ++e) {
+        const uint32_t w = __ldg(a.g.adj + e);
+        const uint32_t wt = a.weighted ? __ldg(a.g.wt + e) : 1u;
+        if (!tight(du, wt, dist_of(a, q, w))) continue;
+        const double now = atomicAdd(a.sigma + row + w, su) + su;
+        smax = now > smax ? now : smax;
+        if (atomicSub(a.pc + row + w, 1u) == 1u) {
+          const uint32_t pos = end + atomicAdd(&s_cnt[(waves + 1) % 3], 1u);
+          if (pos < (uint32_t)n) wl[pos] = w;
+          else raise_status(a.ctrl, FG_ERR_INVALID_ARG, kSiteArena);  // cannot happen: each vertex is released once
+        }
+      }
+    }
+    __syncthreads();
+    const uint32_t added = s_cnt[(waves + 1) % 3];
+    beg = end;
+    end = end + added;
+    ++waves;
+    if (tid == 0) wo[waves + 1] = end;
+  }
+  // largest path count, 2^53 flag, waves: one atomic per block
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double y = __shfl_xor_sync(kFull, smax, o);
+    smax = y > smax ? y : smax;
+  }
+  if (lane == 0) s_red[warp] = smax;
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int w = 0; w < kBcBlockThreads / 32; ++w) m = s_red[w] > m ? s_red[w] : m;
+    if (m > 0.0) atomicMax(&a.cn->sigma_max, (unsigned long long)__double_as_longlong(m));
+    if (m >= kExactLimit) atomicExch(&a.cn->inexact, 1ull);
+    atomicMax(&a.cn->waves, (unsigned long long)waves);
+  }
+  // backward waves: dependencies in CSR order
+  for (int32_t t = (int32_t)waves - 1; t >= 0; --t) {
+    const uint32_t b = __ldcg(wo + t), f = __ldcg(wo + t + 1);
+    for (uint32_t i = b + tid; i < f; i += kBcBlockThreads) {
+      const uint32_t u = __ldcg(wl + i);
+      const double su = __ldcg(a.sigma + row + u);
+      const uint32_t du = dist_of(a, q, u);
+      const uint32_t e0 = __ldg(a.g.rp + u), e1 = __ldg(a.g.rp + u + 1);
+      double acc = 0.0;
+      for (uint32_t e = e0; e < e1; ++e) {
+        const uint32_t w = __ldg(a.g.adj + e);
+        const uint32_t wt = a.weighted ? __ldg(a.g.wt + e) : 1u;
+        if (!tight(du, wt, dist_of(a, q, w))) continue;
+        acc = __dadd_rn(acc, dep_term(su, __ldcg(a.sigma + row + w), __ldcg(a.delta + row + w)));
+      }
+      __stcg(a.delta + row + u, acc);
+    }
+    __syncthreads();
+  }
+}
+
+// bc(v) over the sources in batch order (after bc_block_kernel).
+__global__ void __launch_bounds__(256) bc_gather_kernel(BcArgs a) {
+  const int64_t n = a.g.n;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = a.g.orig ? __ldg(a.g.orig + u) : (int32_t)u;
+    double acc = a.accumulate ? a.bc[v] : 0.0;
+    for (int32_t q = 0; q < a.nq; ++q)
+      if (__ldg(a.src + q) != v) acc = __dadd_rn(acc, __ldcg(a.delta + (int64_t)q * n + u));
+    a.bc[v] = acc;
+  }
+}
+
 }  // namespace
 }  // namespace fg
 
@@ -341,7 +479,7 @@ extern "C" fg_status fg_bc_accumulate(fg_graph *g, const int32_t *src, int32_t n
   CUDA_TRY(w.pc.reserve(cells * sizeof(uint32_t)));
   CUDA_TRY(w.sigma.reserve(cells * sizeof(double)));
   CUDA_TRY(w.delta.reserve(cells * sizeof(double)));
-  CUDA_TRY(w.wave.reserve(cells * sizeof(uint2)));
+  CUDA_TRY(w.wave.reserve(cells * sizeof(uint2) + (size_t)nq * 2 * sizeof(uint32_t)));  // + wave starts (block mode)
   if (g->dg.orig) CUDA_TRY(w.dint.reserve(cells * sizeof(uint32_t)));
   CUDA_TRY(w.wave_off.reserve(((size_t)n + 3) * sizeof(uint32_t)));
   CUDA_TRY(w.ctrl.reserve(sizeof(Ctrl) + sizeof(BcCounters)));
@@ -370,8 +508,19 @@ extern "C" fg_status fg_bc_accumulate(fg_graph *g, const int32_t *src, int32_t n
   a.cn = reinterpret_cast<BcCounters *>(w.ctrl.as<unsigned char>() + sizeof(Ctrl));
   a.watchdog_ns = 60ull * 1000000000ull;
   CUDA_TRY(cudaMemsetAsync(a.ctrl, 0, sizeof(Ctrl) + sizeof(BcCounters), stream));
-  void *args[] = {&a};
-  CUDA_TRY(cudaLaunchCooperativeKernel(bc_kernel, dim3(g->bc_blocks), dim3(kBcThreads), args, 0, stream));
+  if (g->max_degree <= kRoadDegree) {
+    // road-like: deep DAGs with narrow wavefronts, one block per source
+    bc_block_kernel<<<(unsigned)nq, kBcBlockThreads, 0, stream>>>(a);
+    CUDA_TRY(cudaGetLastError());
+    int sms = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t gblocks = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8));
+    bc_gather_kernel<<<(unsigned)gblocks, 256, 0, stream>>>(a);
+    CUDA_TRY(cudaGetLastError());
+  } else {
+    void *args[] = {&a};
+    CUDA_TRY(cudaLaunchCooperativeKernel(bc_kernel, dim3(g->bc_blocks), dim3(kBcThreads), args, 0, stream));
+  }
   unsigned char hb[sizeof(Ctrl) + sizeof(BcCounters)];
   CUDA_TRY(cudaMemcpyAsync(hb, a.ctrl, sizeof(hb), cudaMemcpyDeviceToHost, stream));
   CUDA_TRY(cudaStreamSynchronize(stream));
