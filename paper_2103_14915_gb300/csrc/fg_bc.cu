@@ -5,8 +5,7 @@
 //
 // Input: the batch's exact distance rows (fg_sssp_batch / fg_bfs_batch
 // output). An arc (u, w) is tight for source s when d(u) + wt(u, w) = d(w);
-// the tight arcs form the shortest-path DAG of s. Per source, in one
-// cooperative launch over all the batch's sources at once:
+// the tight arcs form the shortest-path DAG of s. Per source:
 //   count    tight in-arcs per vertex (atomics over every reachable vertex's
 //            out-arcs);
 //   forward  topological waves over the DAGs: wave 0 holds the sources; a
@@ -19,9 +18,12 @@
 //            CSR order of sigma(u) / sigma(w) * (1 + delta(w)), each operation
 //            rounded as written (no fused multiply-add);
 //   gather   bc(v) += delta_s(v) over the sources s != v, in batch order.
-// The waves of all sources advance together, separated by device-wide
-// barriers (bounded waits); their number is the longest hop count of any
-// source's shortest-path DAG.
+// Two forms run these steps. bc_kernel is one cooperative launch over all the
+// batch's sources: their waves advance together, separated by device-wide
+// barriers (bounded waits), which suits shallow, wide DAGs (social graphs).
+// bc_block_kernel runs one source per block with the block's own barrier
+// between waves, which suits the deep, narrow DAGs of road-like graphs
+// (thousands of waves), and bc_gather_kernel does the gather afterwards.
 #include <algorithm>
 #include <cstdint>
 #include <cstdio>

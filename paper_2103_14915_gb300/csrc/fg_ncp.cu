@@ -8,7 +8,7 @@
 // vol = sum of out-degrees, cut = arcs from S_k to the rest; and, across all
 // queries of the call, the profile NCP(k) = min over queries of phi(S_k).
 //
-// One block per query, nothing in global scratch:
+// One block per query (with few queries, several blocks per query, below):
 //   1. select  one pass over the row: vertex v gets the 64-bit sort key
 //              (~key bits << 32 | v), unique, ascending = key descending then
 //              id ascending; keys that may still be among the `top` smallest
@@ -17,12 +17,20 @@
 //              whenever the next tile might not fit, after which only keys
 //              below the `top`-th are admitted. With the tiles in a scrambled
 //              order about top * (1 + ln(#positive / top)) keys are admitted;
+//              a vertex whose key must round below the threshold is skipped
+//              before the division (an FP32 test with a stated bound);
 //   2. sort    bitonic sort of the kept keys;
 //   3. rank    a shared-memory hash from each chosen vertex's internal id to
-//              its sweep rank; one warp per chosen vertex counts the
-//              neighbours that were ranked before it;
+//              its sweep rank; the neighbours ranked before a vertex are
+//              counted by one lane (light vertex), one warp (medium) or the
+//              whole block (a hub of more than 4,096 arcs);
 //   4. scan    prefix sums of d(v) - 2 * inside(v) and of d(v) give cut and vol
 //              exactly in int64; phi = cut / den in FP64.
+// When there are too few rows to give every SM two blocks, each row is split
+// into segments: a block per segment runs step 1 and leaves its top keys in
+// scratch (from the stream-ordered allocator), and a block per row merges the
+// segments' keys through the same buffer and runs steps 2-4. The kept set
+// does not depend on the split.
 //
 // The row read (p from HBM, 4 B per vertex, float4 loads one tile ahead; the
 // degree table, shared by all queries, mostly from L2) is the traffic; steps
