@@ -452,8 +452,8 @@ fg_status fg_rw_batch(const fg_graph *g, const int32_t *src, int32_t nq, int32_t
  * the order the graph lists them. disc_out: uint32[nq * n], original vertex
  * order, disc_out[q * n + v] = the rank at which v is discovered (0 for the
  * source), UINT32_MAX = not reached. src and disc_out are DEVICE pointers
- * owned by the caller. Scratch of 8 * nq * n bytes (12 * nq * n on a
- * relabelled graph) is kept with the graph. Synchronous: enqueues on `stream`,
+ * owned by the caller. Scratch of about 8.125 * nq * n bytes (12.125 * nq * n
+ * on a relabelled graph) is kept with the graph. Synchronous: enqueues on `stream`,
  * waits, and returns FG_ERR_INVALID_ARG when a source id is outside [0, n)
  * (that query's row is left all UINT32_MAX).
  */

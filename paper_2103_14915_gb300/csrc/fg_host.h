@@ -87,14 +87,16 @@ struct BcWorkspace {
   }
 };
 
-// Scratch of fg_dfs_batch: per query a stack of (vertex, arc to resume from)
-// and, for a relabelled graph, the discovery ranks in internal order.
+// Scratch of fg_dfs_batch: per query a stack of (vertex, arc to resume from),
+// a bitmap of discovered vertices and, for a relabelled graph, the discovery
+// ranks in internal order.
 struct DfsWorkspace {
-  DevBuf stack, disc, flag;
+  DevBuf stack, disc, flag, seen;
   void release_all() {
     stack.release();
     disc.release();
     flag.release();
+    seen.release();
   }
 };
 
