@@ -406,8 +406,10 @@ fg_status fg_ll_query(const uint32_t *labels, int64_t n, int32_t K, const int32_
  *
  * Requirements: weighted = 1 needs a weighted graph with positive weights
  * (FG_ERR_UNSUPPORTED otherwise: a weight-0 arc would tie vertices at equal
- * distance); nq * n < 2^32 (split larger batches; scratch of 32 * nq * n bytes
- * is kept with the graph). src, dist and bc (double[n]) are DEVICE pointers
+ * distance); nq * n < 2^32 (split larger batches; scratch of about 32 * nq * n
+ * bytes is kept with the graph). Graphs whose largest out-degree is at most 64
+ * run one block per source, others one cooperative launch for the batch; the
+ * results are the same. src, dist and bc (double[n]) are DEVICE pointers
  * owned by the caller. Each dist row must start at its source (d = 0 there):
  * otherwise FG_ERR_INVALID_ARG (detected on the device).
  *
