@@ -10,6 +10,9 @@ bc(v) = sum over the sources s != v of delta_s(v), delta_s(v) = sum over pairs
 - a star, all sources: the centre carries every ordered leaf pair;
 - networkx's independent Brandes implementation on small random graphs
   (weighted, unweighted with many tied paths, directed, source subsets);
+- unweighted, all sources: the centralities sum to the number of inner
+  vertices over all ordered pairs' shortest paths, sum of (hops(s, t) - 1),
+  hop counts from scipy;
 - planted mistake 8 (the dependency without its "1 +") fails.
 """
 import numpy as np
@@ -101,3 +104,16 @@ def test_planted_mistake_8_is_caught():
     finally:
         oracle.set_mutation(0)
     assert not np.array_equal(b, np.array([2.0 * i * (n - 1 - i) for i in range(n)]))
+
+
+def test_total_centrality_counts_inner_vertices():
+    sp = pytest.importorskip("scipy.sparse")
+    csg = pytest.importorskip("scipy.sparse.csgraph")
+    for trial in range(4):
+        g = inputs.rmat(7, 3, seed=220 + trial)
+        m = sp.csr_matrix((np.ones(g.m), g.col, g.row_ptr), shape=(g.n, g.n))
+        hops = csg.shortest_path(m, unweighted=True, directed=True)
+        reach = np.isfinite(hops) & (hops > 0)
+        b, _, exact = oracle.bc(g, np.arange(g.n), False)
+        assert exact
+        np.testing.assert_allclose(b.sum(), (hops[reach] - 1).sum(), rtol=1e-12)

@@ -9,6 +9,8 @@
 - a vertex without out-arcs ends the walk (-1 afterwards);
 - a star: walks alternate between the centre and leaves, and the leaves are
   chosen uniformly (a frequency check);
+- long walks on a connected non-bipartite undirected graph visit each vertex
+  with frequency close to the stationary d(v) / 2m;
 - planted mistake 9 (output k - 1 drawn) fails the counter pin.
 """
 from pathlib import Path
@@ -88,3 +90,14 @@ def test_planted_mistake_9_is_caught():
             test_counter_scheme(0)
     finally:
         oracle.set_mutation(0)
+
+
+def test_long_walks_approach_the_stationary_distribution():
+    # a connected, non-bipartite undirected graph: a cycle of 11 with chords and a triangle
+    edges = [(i, (i + 1) % 11) for i in range(11)] + [(0, 5), (2, 8), (3, 7), (4, 9), (0, 2)]
+    g = inputs.from_edges(11, edges)
+    deg = np.diff(g.row_ptr).astype(np.float64)
+    paths = oracle.rw(g, np.arange(11, dtype=np.int32).repeat(40), 2000, 4242)
+    visits = np.bincount(paths[:, 200:].ravel(), minlength=g.n).astype(np.float64)  # after a burn-in
+    freq = visits / visits.sum()
+    np.testing.assert_allclose(freq, deg / deg.sum(), atol=0.004)
