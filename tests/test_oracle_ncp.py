@@ -1,5 +1,6 @@
 """Pins of the oracle's sweep cut (the NCP step over PPR vectors): brute force over explicit vertex
-sets on small graphs, a closed form on two cliques joined by a bridge, and a planted mistake."""
+sets on small graphs, a closed form on two cliques joined by a bridge, zero conductance once the
+sweep covers the seed's whole (smaller) component, and a planted mistake."""
 import numpy as np
 import pytest
 
@@ -67,3 +68,18 @@ def test_planted_mistake_is_caught():
     assert not np.array_equal(bad_phi, ok_phi)
     _, ref_phi = _brute(g, p, 10)
     assert np.array_equal(ok_phi[0], np.array(ref_phi))
+
+
+def test_sweep_reaches_zero_conductance_at_the_seed_component():
+    # two components: a 5-cycle with a chord (seeded) and a larger grid; PPR from the
+    # cycle never leaves it, so the prefix that covers the cycle has no cut arcs
+    cyc = [(i, (i + 1) % 5) for i in range(5)] + [(0, 2)]
+    grid = inputs.grid(8, 8, 0, 0, seed=1)
+    edges = cyc + [(5 + int(u), 5 + int(grid.col[e])) for u in range(grid.n)
+                   for e in range(grid.row_ptr[u], grid.row_ptr[u + 1]) if u < grid.col[e]]
+    g = inputs.from_edges(5 + grid.n, edges)
+    p = oracle.ppr_push(g, 0, 0.15, 1e-8)[0].astype(np.float32)
+    assert np.all(p[5:] == 0) and np.all(p[:5] > 0)
+    order, phi, count = oracle.ncp_sweep(g, p[None, :], 64)
+    assert count[0] == 5 and sorted(order[0, :5].tolist()) == [0, 1, 2, 3, 4]
+    assert phi[0, 4] == 0.0 and np.all(phi[0, :4] > 0.0)
