@@ -3,14 +3,20 @@
 Plain, slow reference implementations of the per-source queries of the
 fork-processing pattern (Alg. 1, Def. 2.2): Dijkstra SSSP, queue BFS levels,
 FP64 power-iteration PPR and an FP64 sequential push, plus implementation-free
-certificate checks. Only ``tests/``, ``__graft_entry__.smoke()`` and the
-``cpu_baseline`` / reference legs of ``bench.py`` may import this package. It
-shares no code with the CUDA path and never imports it.
+certificate checks; and of what is built on them: the NCP sweep, landmark
+labels and queries, sampled betweenness centrality (Sec. 1, 6.1), random
+walks and DFS (Sec. 3). Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` (which time this oracle and
+check sampled outputs against it) may import this package. It shares no code
+with the CUDA path and never imports it.
 
 Parity pins (what ties this oracle to something other than itself) live in
-``tests/test_oracle.py``; every function here is pinned there. The PPR
-sequential push (``ppr_push``) is order-dependent by design: its per-vertex
-values are checked only against the error bound, never element by element.
+``tests/test_oracle.py`` (SSSP, BFS, PPR, certificates),
+``tests/test_oracle_ncp.py``, ``test_oracle_ll.py``, ``test_oracle_bc.py``,
+``test_oracle_rw.py``, ``test_oracle_dfs.py`` and the hand-worked fixtures of
+``tests/golden/``; every function here is pinned there. The PPR sequential
+push (``ppr_push``) is order-dependent by design: its per-vertex values are
+checked only against the error bound, never element by element.
 """
 from __future__ import annotations
 
