@@ -34,6 +34,23 @@ def test_exports_every_declared_symbol(lib):
     assert set(names) == set(fg.EXPORTS)
 
 
+def test_every_declaration_is_documented():
+    """Each declared entry point follows a comment block (within the few lines
+    above it, or shares one with the declarations right before it)."""
+    lines = HEADER.read_text().splitlines()
+    undocumented, seen = [], []
+    for i, line in enumerate(lines):
+        m = re.match(r"^(?:fg_status|void|const char|[a-z_0-9]+_t)\s*\*?\s*(fg_[a-z_]+)\s*\(", line)
+        if not m:
+            continue
+        seen.append(m.group(1))
+        window = "\n".join(lines[max(0, i - 12):i])
+        if "*/" not in window:
+            undocumented.append(m.group(1))
+    assert sorted(set(seen)) == declared_functions()
+    assert not undocumented, undocumented
+
+
 def test_struct_sizes_match_header(lib):
     o = fg.fg_default_opts()
     assert o.struct_size == ctypes.sizeof(fg.fg_opts)
