@@ -77,3 +77,13 @@ def test_sources():
     for k, cnt in enumerate(counts):
         if avail[k]:
             assert cnt == min(avail[k], share) or cnt == share - 1
+
+
+def test_ncp_seeds_are_a_seeded_sample_of_non_isolated_vertices():
+    g = I.rmat(16, 8, seed=31)
+    s1 = I.ncp_seeds(g)
+    assert len(s1) == round(1e-4 * g.n) and len(set(s1.tolist())) == len(s1)
+    assert np.all(np.diff(g.row_ptr)[s1] >= 1)
+    assert np.array_equal(s1, I.ncp_seeds(g))             # seeded: the same sample again
+    assert not np.array_equal(s1, I.ncp_seeds(g, seed=8))  # another seed, another sample
+    assert len(I.ncp_seeds(g, fraction=1e-3)) == round(1e-3 * g.n)
