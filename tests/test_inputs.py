@@ -87,3 +87,34 @@ def test_ncp_seeds_are_a_seeded_sample_of_non_isolated_vertices():
     assert np.array_equal(s1, I.ncp_seeds(g))             # seeded: the same sample again
     assert not np.array_equal(s1, I.ncp_seeds(g, seed=8))  # another seed, another sample
     assert len(I.ncp_seeds(g, fraction=1e-3)) == round(1e-3 * g.n)
+
+
+# ---------------------------------------------------------------------------
+# Recorded CSR hashes (tests/golden/csr_sha256.txt, written by
+# tests/golden/make_csr_sha256.py from the generators alone): a generator
+# change between runs changes the workloads, and these pins catch it.
+# The two largest graphs (R-MAT s24 and s25, about a minute and several GB of
+# host memory each) are checked only with FG_LARGE_INPUTS=1; bench.py checks
+# the s24 graph it generates on every run.
+# ---------------------------------------------------------------------------
+import os
+import sys
+from pathlib import Path
+
+import pytest
+
+sys.path.insert(0, str(Path(__file__).resolve().parent / "golden"))
+import make_csr_sha256 as H  # noqa: E402
+
+_LARGE = {"rmat24_sssp", "rmat25_serving"}
+
+
+@pytest.mark.parametrize("name", H.WORKLOADS)
+def test_workload_csr_sha256_matches_record(name):
+    if name in _LARGE and os.environ.get("FG_LARGE_INPUTS") != "1":
+        pytest.skip("large workload graph: set FG_LARGE_INPUTS=1 (bench.py checks R-MAT s24 on every run)")
+    rec = H.read()[name]
+    g = I.workload_graph(name)
+    assert (g.n, g.m) == (rec["n"], rec["m"])
+    assert H.csr_sha256(g) == rec["csr"]
+    assert H.sources_sha256(I.workload_sources(name, g)) == rec["sources"]
