@@ -303,9 +303,12 @@ fg_status fg_server_release(fg_server *s, uint64_t id);
  * which must be the current device. The call makes no cudaMalloc, cudaFree or
  * host allocation, takes no fg_opts, and does not update fg_stats.
  *
- * Set-up: the first call on each device (with that device current) looks up
- * the scratch's device address with cudaGetSymbolAddress and sizes the
- * cooperative grid; make that first call before any stream capture begins.
+ * Set-up: fg_graph_create, on the graph's device, places the scratch array in
+ * device memory (with lazy module loading that happens when its address is
+ * first looked up, with cudaGetSymbolAddress), loads the plain kernel and
+ * sizes its cooperative grid. So the scratch is taken while the device's
+ * memory is still free, and a later fg_sssp_batch_noalloc call adds no device
+ * memory. If that set-up failed, the first call on the device retries it.
  * Each call clears the scratch's control block (a memset on `stream`) before
  * its first launch; nothing else needs to start at zero.
  *

@@ -114,5 +114,7 @@ cudaError_t launch_plain(const PlainArgs &a, int blocks, int threads, cudaStream
 // runtime services for entry points outside fg_runtime.cpp
 fg_status report_error(fg_status s, const char *msg);  // sets fg_last_error(), returns s
 void graph_device_view(const fg_graph *g, DevGraph *dg, int *device);
+// set-up of fg_sssp_batch_noalloc's fixed scratch on device dev (current); best effort
+void noalloc_prepare(int dev);
 
 }  // namespace fg

@@ -43,15 +43,21 @@ struct DeviceSetup {
 std::mutex g_setup_mu;
 DeviceSetup g_setup[kMaxDevices];
 
-char g_msg[256];
-
+// Formats into the caller's stack: calls on different devices may fail at the
+// same time, and each thread's fg_last_error() must carry its own message.
 fg_status fail_msg(fg_status s, const char *fmt, long long a, long long b) {
-  std::snprintf(g_msg, sizeof(g_msg), fmt, a, b);
-  return report_error(s, g_msg);
+  char msg[256];
+  std::snprintf(msg, sizeof(msg), fmt, a, b);
+  return report_error(s, msg);
 }
 
-// First call on a device (that device current): look up the scratch's device
-// address and the plain kernel's cooperative grid. Retried on failure.
+// Set-up of one device (that device current): look up the scratch's device
+// address and the plain kernel's cooperative grid. With lazy module loading
+// (CUDA's default) the lookup is what loads the module and places the scratch
+// array in device memory, and the occupancy query loads the plain kernel; a
+// memset of the control block brings up the runtime's memset path. All of it
+// happens here, once, so that later calls on the device take no memory and
+// load nothing. Retried on failure.
 fg_status setup_device(int dev, const DeviceSetup **out) {
   std::lock_guard<std::mutex> lk(g_setup_mu);
   DeviceSetup &s = g_setup[dev];
@@ -64,16 +70,31 @@ fg_status setup_device(int dev, const DeviceSetup **out) {
     int blocks = 0, threads = 0;
     e = plain_grid_size(&blocks, &threads);
     if (e != cudaSuccess) return report_error(FG_ERR_CUDA, cudaGetErrorString(e));
+    e = cudaMemset(p, 0, sizeof(Ctrl));
+    if (e != cudaSuccess) return report_error(FG_ERR_CUDA, cudaGetErrorString(e));
     s.base = static_cast<unsigned char *>(p);
     s.blocks = blocks;
     s.threads = threads;
     s.done = true;
   }
-  *out = &s;
+  if (out) *out = &s;
   return FG_OK;
 }
 
 }  // namespace
+
+// Called by fg_graph_create on the graph's device (current), so that the
+// scratch is in place before the caller's own pool takes the free memory.
+// A failure here is not an error of graph creation: the first
+// fg_sssp_batch_noalloc call on the device retries and reports it.
+void noalloc_prepare(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) return;
+  if (setup_device(dev, nullptr) != FG_OK) {
+    (void)cudaGetLastError();
+    report_error(FG_OK, "");
+  }
+}
+
 }  // namespace fg
 
 using namespace fg;

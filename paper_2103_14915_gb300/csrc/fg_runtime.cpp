@@ -306,6 +306,10 @@ extern "C" fg_status fg_graph_create_ex(int64_t n, int64_t m, const int64_t *row
   d.wt = wt ? g->wt.as<uint32_t>() : nullptr;
   d.orig = identity ? nullptr : g->orig.as<int32_t>();
   d.intl = identity ? nullptr : g->intl.as<int32_t>();
+  // the no-allocation entry point's scratch is placed on the device now, while
+  // the caller's memory is still free (lazy module loading would otherwise
+  // place it at that entry point's first call)
+  noalloc_prepare(dev);
   *out = g;
   return FG_OK;
 }

@@ -122,3 +122,21 @@ def test_host_side_argument_checks():
         assert fg.fg_sssp_batch_noalloc(h, s_d, 2, out.data_ptr() + 2) == fg.FG_ERR_INVALID_ARG
     finally:
         fg.fg_graph_destroy(h)
+
+
+def test_call_after_graph_creation_adds_no_device_memory():
+    # graph creation placed the scratch; the call itself must take nothing
+    g = inputs.rmat(10, 8, seed=21, weights=(1, 255))
+    h = _create(g, fg.FG_PART_RANGE, 64)
+    try:
+        s_d = torch.from_numpy(inputs.sources_uniform(g, 3, seed=2).astype(np.int32)).to(DEV)
+        out = torch.empty((3, g.n), dtype=torch.int32, device=DEV)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        fg.check(fg.fg_sssp_batch_noalloc(h, s_d, 3, out))
+        free1 = torch.cuda.mem_get_info()[0]
+        assert free1 == free0
+        assert torch.equal(out, _batch(h, g, s_d))
+    finally:
+        fg.fg_graph_destroy(h)
+
