@@ -102,21 +102,40 @@ typedef struct {
     int32_t threads_per_vertex; /* SSSP/BFS expansion: 1 = one lane per frontier vertex (graphs
                                with out-degree <= 8 only), 32 or 0 (default) = a warp shares
                                a batch of 32 frontier vertices' arcs evenly */
+    int32_t group;          /* SSSP/BFS queries that share one partition visit lane by lane
+                               (the query group): 8, 16 or 32 = the group engine, whose state
+                               keeps a group's values of one vertex in one line, so one access
+                               and one read of the arcs serve the whole group (best where almost
+                               every arc leaves its partition: power-law graphs); 1 = one query
+                               per warp and visit (best on road-like graphs, whose partitions
+                               keep most arcs inside). 0 (default) = automatic: 16 when more
+                               than half of the graph's arcs cross partitions, else 1. PPR
+                               always runs one query per warp. In the group engine, sched_window
+                               (SSSP) bounds each round to values below the group's smallest
+                               pending value plus the window; delta, bucket, yield_edges,
+                               emit_capacity and threads_per_vertex do not apply */
 } fg_opts;
 
 /* counters of the last completed batch on a graph (read by fg_stats after fg_sync) */
 typedef struct {
     uint64_t rounds;        /* Alg. 2 loop iterations (sum over launches) */
-    uint64_t visits;        /* (partition, query) buffers processed */
-    uint64_t edges;         /* arcs scanned by the relax/push kernels */
-    uint64_t ops;           /* operations buffered */
+    uint64_t visits;        /* (partition, query) buffers processed; group engine: (partition,
+                               group) items and hub chunks */
+    uint64_t edges;         /* arcs scanned by the relax/push kernels, counted per query (a
+                               group engine arc counts once per lane it relaxes) */
+    uint64_t ops;           /* operations buffered; group engine: target values lowered */
     uint64_t spills;        /* expansions deferred because the op arena was full */
     uint64_t yields;        /* visits that left work behind (yield or budget) */
     uint64_t launches;      /* kernels launched by the batch */
     uint64_t max_round_ops; /* most operations buffered in one round */
     uint64_t phase_ns[6];   /* device time per phase, summed over rounds, between device-wide
                                barriers: tile init, seeding, scan A, scan B (scheduling),
-                               scatter into bins, intra-partition processing */
+                               scatter into bins, intra-partition processing (the group engine
+                               uses tile init, seeding, scan (in slot 2) and processing) */
+    uint64_t arcs_read;     /* arcs read from the graph: per (arc, query) visit with one query
+                               per warp, per (arc, group) with the group engine, where one read
+                               serves every lane of the group */
+    uint64_t group;         /* queries per group of the last launch (1 = one query per warp) */
 } fg_stats_t;
 
 typedef struct {
@@ -204,15 +223,19 @@ fg_status fg_partition_plan(int64_t n, const int64_t *row_ptr, const int32_t *co
 enum { FG_QUERY_SSSP = 0, FG_QUERY_BFS = 1, FG_QUERY_PPR = 2 };
 
 /*
- * Schedule autotuner. The paper tunes its scheduling and yield parameters by
- * hand per graph (Sec. 5, Tab. 4); here the host times candidate fg_opts for
- * one query kind (FG_QUERY_*, declared below) on a sample batch and writes the
- * fastest to *best: the default (FIFO), then FG_SCHED_PRIORITY windows from
+ * Autotuner. The paper tunes its scheduling and yield parameters by hand per
+ * graph (Sec. 5, Tab. 4); here the host times candidate fg_opts for one query
+ * kind (FG_QUERY_*, declared below) on a sample batch and writes the fastest
+ * to *best: the default; for SSSP and BFS the query group (1, 16 or 32; see
+ * fg_opts.group); then, with one query per warp, FG_SCHED_PRIORITY windows from
  * wide to narrow -- multiples of the graph's mean arc weight for SSSP, levels
- * for BFS -- until one takes more than twice the best time, then delta (yield
- * heuristic 2) of half and a quarter of the best window, then, on graphs with
- * out-degree <= 8, lane-per-vertex expansion. PPR keeps
- * the default. src: DEVICE int32[nq] (the sample; a few hundred sources is
+ * for BFS -- until one takes more than twice the best time, delta (yield
+ * heuristic 2) of half and a quarter of the best window, and on graphs with
+ * out-degree <= 8 lane-per-vertex expansion; with the group engine, SSSP
+ * windows of 16 and 4 mean weights; last, for every kind with nq >= 64, half
+ * the batch per launch (query_batch). PPR keeps FIFO scheduling. best->group
+ * is never 0: the automatic choice is resolved. The partition size is a graph
+ * property: compare graphs created with different partition_vertices. src: DEVICE int32[nq] (the sample; a few hundred sources is
  * typical). The tuner allocates nq * n * 4 B of output rows for the duration
  * of the call and runs each candidate once on `stream` (it synchronises).
  * report (nullable) receives the number of candidates and the default's and
@@ -228,6 +251,15 @@ typedef struct {
 
 fg_status fg_tune_opts(fg_graph *g, int32_t kind, const int32_t *src, int32_t nq, void *stream,
                        fg_opts *best, fg_tune_report *report);
+
+/*
+ * As fg_tune_opts, with the PPR parameters the caller will use (fg_tune_opts
+ * times PPR candidates at alpha = 0.15, eps = 1e-6). For PPR the choice is
+ * cached per (batch-size bucket, alpha, eps). alpha and eps are ignored for
+ * SSSP and BFS. Requires 0 < alpha < 1 and eps > 0 for PPR.
+ */
+fg_status fg_tune_opts_ex(fg_graph *g, int32_t kind, const int32_t *src, int32_t nq, float alpha, float eps,
+                          void *stream, fg_opts *best, fg_tune_report *report);
 
 /*
  * Serving loop (continuous batching). Requests -- one SSSP, BFS or PPR query

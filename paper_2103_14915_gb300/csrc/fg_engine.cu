@@ -1196,6 +1196,7 @@ done:
     if (lane == 0) {
       atomicAdd(&c->visits, ctr.visits);
       atomicAdd(&c->edges, ctr.edges);
+      atomicAdd(&c->arcs_read, ctr.edges);
       atomicAdd(&c->spills, sp);
       atomicAdd(&c->yields, yl);
     }

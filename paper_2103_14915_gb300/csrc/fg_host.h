@@ -63,6 +63,7 @@ struct IoSlot {
 
 struct Workspace {
   DevBuf cnt, prio, dirty, cur, pend, qbest, items, iprio, blocksum, e_key, e_op, b_op, ctrl;
+  DevBuf g_D, g_pend, g_dirty, g_items, g_best;  // group engine
   DevBuf scratch_r, scratch_c, scratch_p, state;
   DevBuf pl_dist, pl_rr, pl_pp, pl_cc, pl_stamp, pl_f0, pl_f1, pl_sizes;
   IoSlot io[2];
@@ -71,7 +72,8 @@ struct Workspace {
   void release_all() {
     DevBuf *all[] = {&cnt, &prio, &dirty, &cur, &pend, &qbest, &items, &iprio, &blocksum, &e_key, &e_op,
                      &b_op, &ctrl, &scratch_r, &scratch_c, &scratch_p, &state, &pl_dist, &pl_rr,
-                     &pl_pp, &pl_cc, &pl_stamp, &pl_f0, &pl_f1, &pl_sizes};
+                     &pl_pp, &pl_cc, &pl_stamp, &pl_f0, &pl_f1, &pl_sizes, &g_D, &g_pend, &g_dirty,
+                     &g_items, &g_best};
     for (DevBuf *b : all) b->release();
     io[0].release();
     io[1].release();
@@ -97,6 +99,17 @@ struct DfsWorkspace {
     disc.release();
     flag.release();
     seen.release();
+  }
+};
+
+struct TuneKey {
+  int kind, bucket;
+  uint32_t alpha_bits, eps_bits;
+  bool operator<(const TuneKey &o) const {
+    if (kind != o.kind) return kind < o.kind;
+    if (bucket != o.bucket) return bucket < o.bucket;
+    if (alpha_bits != o.alpha_bits) return alpha_bits < o.alpha_bits;
+    return eps_bits < o.eps_bits;
   }
 };
 
@@ -128,12 +141,24 @@ struct fg_graph {
   int engine_qtype = -1;
   uint32_t max_degree = 0;
   double mean_weight = 1.0;        // mean arc weight (1 when unweighted)
-  // schedules chosen by fg_tune_opts, keyed by (query kind, log2 of the batch size rounded up)
-  std::map<std::pair<int, int>, std::pair<fg_opts, fg_tune_report>> tuned;
+  // choices of fg_tune_opts[_ex], keyed by (query kind, log2 of the batch size
+  // rounded up, and for PPR the bits of alpha and eps)
+  std::map<fg::TuneKey, std::pair<fg_opts, fg_tune_report>> tuned;
   int plain_blocks = 0, plain_threads = 0;
+  // group engine: the hubs, vertices with more than kHubMin arcs (internal ids),
+  // relaxed in chunks of at most kHubChunk arcs spread over blocks, and the
+  // number of chunks they make; launch shapes per group size (index log2(G) - 3)
+  fg::DevBuf hubs;
+  int32_t nhubs = 0;
+  uint64_t hub_chunks = 0;
+  int group_blocks[3] = {0, 0, 0}, group_threads[3] = {0, 0, 0};
+  size_t group_smem[3] = {0, 0, 0};
 };
 
 namespace fg {
+
+constexpr uint32_t kHubMin = 512;     // group engine: vertices with more arcs are hubs
+constexpr uint32_t kHubChunk = 4096;  // group engine: arcs per hub chunk
 
 // One batch of nq queries on workspace ws (see fg_runtime.cpp).
 fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div, int qtype, const int32_t *src_in,

@@ -15,8 +15,7 @@ constexpr uint32_t kInf = 0xFFFFFFFFu;
 constexpr uint32_t kInvalidKey = 0xFFFFFFFFu;
 
 // where a device status was raised (reported by fg_sync)
-// (site 2 is unused: it named a shared-memory staging wait that no longer exists)
-enum : unsigned { kSiteNone = 0, kSiteBarrier = 1, kSiteUnused2 = 2, kSiteVisit = 3, kSiteRounds = 4,
+enum : unsigned { kSiteNone = 0, kSiteBarrier = 1, kSiteStage = 2, kSiteVisit = 3, kSiteRounds = 4,
                   kSiteSource = 5, kSiteArena = 6, kSiteDegree = 7, kSiteClaim = 8 };
 
 // Graph in partition-major ("internal") vertex order. Partition j holds the
@@ -46,6 +45,10 @@ struct Ctrl {
   unsigned long long e_cursor;  // operations reserved in the arena this round
   unsigned long long rounds, visits, edges, ops, spills, yields, max_round_ops;
   unsigned long long phase_ns[6];  // K0, INIT, SCAN-A, SCAN-B, SCATTER, PROCESS (block 0's view)
+  // group engine: per round parity, the items found by the scan (hub chunks,
+  // partition items) and the claiming counter
+  unsigned int g_hub_items[2], g_items[2], g_next[2];
+  unsigned long long arcs_read;  // graph arcs read (per query visit, or per group visit)
 };
 
 struct EngineArgs {
@@ -83,6 +86,35 @@ struct EngineArgs {
   uint32_t lanes = 0;  // 1: lane-per-vertex expansion (max out-degree <= 8)
 };
 
+// Group engine (fg_group.cu): G queries per group, lanes = queries. State is
+// vertex-major inside a group, D[group][vertex][G] in internal order, so the
+// G values of one vertex are one contiguous line. A vertex whose value was
+// lowered in round r is marked in pend[(r + 1) & 1][group][vertex] (a mask of
+// G bits) and its partition in dirty[(r + 1) & 1][group * nparts + p].
+struct GroupArgs {
+  DevGraph g;
+  int qtype = Q_SSSP;
+  int32_t nq = 0;
+  int32_t G = 16;                 // queries per group: 8, 16 or 32
+  int32_t glog2 = 4;              // log2(G)
+  int32_t ngroups = 0;            // ceil(nq / G)
+  int64_t npad = 0;               // nparts * S: vertices per group row, padded to whole partitions
+  const int32_t *src = nullptr;   // [nq] original ids (device)
+  uint32_t *D = nullptr;          // [ngroups][npad][G]
+  uint32_t *pend = nullptr;       // [2][ngroups][npad] G-bit masks
+  uint32_t *dirty = nullptr;      // [2][ngroups * nparts]
+  uint4 *items = nullptr;         // [hub_cap + ngroups * nparts]
+  uint32_t hub_cap = 0;           // item slots reserved for hub chunks
+  const uint32_t *hubs = nullptr; // [nhubs] internal ids of the hubs (vertices with many arcs)
+  int32_t nhubs = 0;
+  uint32_t hub_chunk = 4096;      // arcs per hub chunk (a work item of its own)
+  uint32_t window = 0;            // per-group value window of a round (0 = none)
+  uint32_t *gbest = nullptr;      // [2][ngroups] smallest pending value per group (window scheduling)
+  Ctrl *ctrl = nullptr;
+  uint32_t max_rounds = 0;
+  uint64_t watchdog_ns = 0;
+};
+
 struct PlainArgs {
   DevGraph g;
   int qtype = Q_SSSP;
@@ -109,6 +141,10 @@ cudaError_t launch_ppr_finalize(const EngineArgs &a, double *mass, float *p_out,
 cudaError_t launch_permute_out(const uint32_t *state, uint32_t *out, const int32_t *orig, int64_t n, int64_t rows,
                                cudaStream_t s);
 cudaError_t plain_grid_size(int *blocks, int *threads);
+cudaError_t group_grid_size(int S, int G, int *blocks, int *threads, size_t *smem);
+cudaError_t launch_group(const GroupArgs &a, int blocks, int threads, size_t smem, cudaStream_t s);
+// group-engine state (internal order, vertex-major in groups) -> caller's query-major rows
+cudaError_t launch_group_out(const GroupArgs &a, uint32_t *out, cudaStream_t s);
 cudaError_t launch_plain(const PlainArgs &a, int blocks, int threads, cudaStream_t s);
 
 // runtime services for entry points outside fg_runtime.cpp

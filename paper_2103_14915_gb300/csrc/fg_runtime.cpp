@@ -44,6 +44,7 @@ struct Pending {
   Workspace *ws;  // workspace the batch ran on (its pending bitmaps need a reset after an abort)
   Ctrl *host;     // pinned copy of the device control block
   unsigned launches;
+  unsigned group;  // queries per group of the batch's launches
 };
 
 std::mutex g_pending_mu;
@@ -252,6 +253,7 @@ extern "C" fg_status fg_graph_create_ex(int64_t n, int64_t m, const int64_t *row
   g->device = dev;
   auto cleanup = [&](fg_status s) {
     g->rp.release(); g->adj.release(); g->wt.release(); g->orig.release(); g->intl.release();
+    g->hubs.release();
     delete g;
     return s;
   };
@@ -284,7 +286,20 @@ extern "C" fg_status fg_graph_create_ex(int64_t n, int64_t m, const int64_t *row
     }
     if (m > 0) g->mean_weight = sum / (double)m;
   }
-  for (int64_t v = 0; v < n; ++v) g->max_degree = std::max(g->max_degree, i_rp[(size_t)v + 1] - i_rp[(size_t)v]);
+  std::vector<uint32_t> hubs;
+  for (int64_t v = 0; v < n; ++v) {
+    const uint32_t deg = i_rp[(size_t)v + 1] - i_rp[(size_t)v];
+    g->max_degree = std::max(g->max_degree, deg);
+    if (deg > kHubMin) {
+      hubs.push_back((uint32_t)v);
+      g->hub_chunks += (deg + kHubChunk - 1) / kHubChunk;
+    }
+  }
+  g->nhubs = (int32_t)hubs.size();
+  if (!hubs.empty()) {
+    CUDA_TRY_G(g->hubs.reserve(sizeof(uint32_t) * hubs.size()));
+    CUDA_TRY_G(cudaMemcpy(g->hubs.p, hubs.data(), sizeof(uint32_t) * hubs.size(), cudaMemcpyHostToDevice));
+  }
   if (!identity) {
     CUDA_TRY_G(g->orig.reserve(sizeof(int32_t) * (size_t)n));
     CUDA_TRY_G(g->intl.reserve(sizeof(int32_t) * (size_t)n));
@@ -331,6 +346,7 @@ extern "C" fg_status fg_graph_destroy(fg_graph *g) {
     g->ws.release_all();
     g->rp.release(); g->adj.release(); g->wt.release(); g->orig.release(); g->intl.release();
     g->deg.release();
+    g->hubs.release();
     g->bc.release_all();
     g->dfs.release_all();
     if (g->last_done) cudaEventDestroy(g->last_done);
@@ -452,6 +468,8 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
   if (o.host_io < 0 || o.host_io > 2) return fail(FG_ERR_INVALID_ARG, "host_io must be 0, 1 or 2");
   if (o.threads_per_vertex != 0 && o.threads_per_vertex != 1 && o.threads_per_vertex != 32)
     return fail(FG_ERR_INVALID_ARG, "threads_per_vertex must be 0, 1 or 32");
+  if (o.group != 0 && o.group != 1 && o.group != 8 && o.group != 16 && o.group != 32)
+    return fail(FG_ERR_INVALID_ARG, "group must be 0, 1, 8, 16 or 32");
   if (qtype == Q_PPR) o.sched = FG_SCHED_FIFO;  // PPR buffers are scheduled first-in first-out
   const uint32_t max_rounds = o.max_rounds ? o.max_rounds : 1000000u;
   const uint64_t watchdog_ns = (uint64_t)(o.watchdog_ms ? o.watchdog_ms : 30000u) * 1000000ull;
@@ -507,7 +525,14 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
     const double per_query = (double)g->nparts * 36.0 + (double)n / 8.0 +
                              (qtype == Q_PPR ? (relabelled ? 12.0 : (need_r ? 8.0 : 4.0)) * (double)n
                                              : (relabelled ? 4.0 : 0.0) * (double)n);
-    const double budget = 24e9;
+    // the device's free memory (plus what this workspace already holds, which a
+    // regrow frees first), less a margin; the arena is sized separately below
+    size_t free_b = 0, total_b = 0;
+    CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    const size_t held = ws.cnt.bytes + ws.prio.bytes + ws.dirty.bytes + ws.cur.bytes + ws.pend.bytes +
+                        ws.items.bytes + ws.iprio.bytes + ws.scratch_r.bytes + ws.scratch_c.bytes +
+                        ws.scratch_p.bytes + ws.state.bytes;
+    const double budget = std::max(0.0, 0.8 * (double)(free_b + held) - 12e9);
     const int64_t cap_q = std::max<int64_t>(1, (int64_t)(budget / per_query));
     nb = std::min<int64_t>(nb, cap_q);
     const int64_t key_cap = (int64_t)((0xFFFFFFFEull) / (uint64_t)g->nparts);
@@ -516,8 +541,81 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
   }
   int launches = 0;
   Ctrl *d_ctrl = nullptr;
+  // query group: one lane per query (group engine) where most arcs leave their
+  // partition, else one warp per query and visit; PPR is never grouped
+  int Gq = 1;
+  if (qtype != Q_PPR && o.mode == FG_MODE_BUFFERED) {
+    if (o.group == 0) Gq = (g->m > 0 && 2 * g->cut > g->m) ? 16 : 1;
+    else Gq = o.group;
+  }
 
-  if (o.mode == FG_MODE_BUFFERED) {
+  if (o.mode == FG_MODE_BUFFERED && Gq > 1) {
+    int glog2 = 0;
+    while ((1 << glog2) < Gq) ++glog2;
+    const int64_t npad = (int64_t)g->nparts * (int64_t)g->S;
+    // queries per launch from the device's free memory: per group the state
+    // (G values per vertex), two pending masks per vertex, the dirty flags and
+    // work items of its partitions and its hub chunks
+    int64_t nbq = o.query_batch ? o.query_batch : nq;
+    {
+      size_t free_b = 0, total_b = 0;
+      CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+      const size_t held = ws.g_D.bytes + ws.g_pend.bytes + ws.g_dirty.bytes + ws.g_items.bytes + ws.g_best.bytes;
+      const double avail = 0.9 * (double)(free_b + held) - 512.0 * 1024 * 1024;
+      const double per_group = (double)npad * 4.0 * (double)Gq + 8.0 * (double)npad + 24.0 * (double)g->nparts +
+                               16.0 * (double)g->hub_chunks + 8.0;
+      int64_t cap_groups = std::max<int64_t>(1, (int64_t)(avail / per_group));
+      const int64_t key_cap = (int64_t)(0xFFFFFFF0ull / (uint64_t)g->nparts);
+      cap_groups = std::min<int64_t>(cap_groups, key_cap);
+      nbq = std::min<int64_t>(nbq, cap_groups * Gq);
+      nbq = std::min<int64_t>(nbq, nq);
+    }
+    const int gi = glog2 - 3;
+    if (g->group_blocks[gi] == 0)
+      CUDA_TRY(group_grid_size(g->S, Gq, &g->group_blocks[gi], &g->group_threads[gi], &g->group_smem[gi]));
+    const int blocks = grid_div > 1 ? std::max(1, g->group_blocks[gi] / grid_div) : g->group_blocks[gi];
+    const int64_t ngroups_max = (nbq + Gq - 1) / Gq;
+    const uint64_t hub_cap = (uint64_t)ngroups_max * g->hub_chunks;
+    if (hub_cap + (uint64_t)ngroups_max * (uint64_t)g->nparts >= 0xFFFFFFFFull)
+      return fail(FG_ERR_UNSUPPORTED, "too many work items for one launch; lower query_batch");
+    CUDA_TRY(ws.g_D.reserve(4 * (size_t)ngroups_max * (size_t)npad * (size_t)Gq));
+    CUDA_TRY(ws.g_pend.reserve(8 * (size_t)ngroups_max * (size_t)npad));
+    CUDA_TRY(ws.g_dirty.reserve(8 * (size_t)ngroups_max * (size_t)g->nparts));
+    CUDA_TRY(ws.g_items.reserve(16 * (size_t)(hub_cap + (uint64_t)ngroups_max * (uint64_t)g->nparts)));
+    CUDA_TRY(ws.g_best.reserve(8 * (size_t)ngroups_max));
+    CUDA_TRY(ws.ctrl.reserve(sizeof(Ctrl)));
+    d_ctrl = ws.ctrl.as<Ctrl>();
+    CUDA_TRY(cudaMemsetAsync(d_ctrl, 0, sizeof(Ctrl), stream));
+    for (int64_t q0 = 0; q0 < nq; q0 += nbq) {
+      const int64_t cnt_q = std::min<int64_t>(nbq, nq - q0);
+      GroupArgs a;
+      a.g = g->dg;
+      a.qtype = qtype;
+      a.nq = (int32_t)cnt_q;
+      a.G = Gq;
+      a.glog2 = glog2;
+      a.ngroups = (int32_t)((cnt_q + Gq - 1) / Gq);
+      a.npad = npad;
+      a.src = src + q0;
+      a.D = ws.g_D.as<uint32_t>();
+      a.pend = ws.g_pend.as<uint32_t>();
+      a.dirty = ws.g_dirty.as<uint32_t>();
+      a.items = ws.g_items.as<uint4>();
+      a.hub_cap = (uint32_t)((uint64_t)a.ngroups * g->hub_chunks);
+      a.hubs = g->nhubs ? g->hubs.as<uint32_t>() : nullptr;
+      a.nhubs = g->nhubs;
+      a.hub_chunk = kHubChunk;
+      a.window = qtype == Q_SSSP && o.sched == FG_SCHED_PRIORITY ? o.sched_window : 0u;
+      a.gbest = a.window ? ws.g_best.as<uint32_t>() : nullptr;
+      a.ctrl = d_ctrl;
+      a.max_rounds = max_rounds;
+      a.watchdog_ns = watchdog_ns;
+      CUDA_TRY(launch_group(a, blocks, g->group_threads[gi], g->group_smem[gi], stream));
+      ++launches;
+      CUDA_TRY(launch_group_out(a, dist + (size_t)q0 * (size_t)n, stream));
+      ++launches;
+    }
+  } else if (o.mode == FG_MODE_BUFFERED) {
     const uint64_t K = (uint64_t)g->nparts * (uint64_t)nb;
     // the arena holds every seed operation of a launch; beyond that a round
     // stops at 3/4 of it (arena pressure) and overflow spills losslessly into
@@ -665,7 +763,7 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
   }
   {
     std::lock_guard<std::mutex> lp(g_pending_mu);
-    g_pending.push_back(Pending{stream, g, &ws, h, (unsigned)launches});
+    g_pending.push_back(Pending{stream, g, &ws, h, (unsigned)launches, (unsigned)Gq});
   }
   if (host_io) {
     if (qtype == Q_PPR) {
@@ -741,13 +839,15 @@ extern "C" fg_status fg_sync(void *stream_v) {
       s.launches = p.launches;
       s.max_round_ops = c.max_round_ops;
       for (int k = 0; k < 6; ++k) s.phase_ns[k] = c.phase_ns[k];
+      s.arcs_read = c.arcs_read;
+      s.group = p.group;
       p.graph->last_stats = s;
       if (c.status != 0 && c.status != FG_ERR_OVERFLOW && p.ws) p.ws->pend_clean = false;
     }
     if (first == FG_OK && c.status != 0) {
       const char *names[] = {"ok", "invalid argument", "out of memory", "CUDA error", "watchdog timeout",
                              "operation buffer overflow", "distance overflow", "unsupported"};
-      const char *sites[] = {"", " (device-wide barrier wait)", "",
+      const char *sites[] = {"", " (device-wide barrier wait)", " (shared-memory staging wait)",
                              " (visit step limit)", " (max_rounds)", " (source id out of range)",
                              " (operation arena)", " (vertex degree out of range)", " (work-item claim wait)"};
       const int k = c.status >= 0 && c.status <= 7 ? c.status : 3;

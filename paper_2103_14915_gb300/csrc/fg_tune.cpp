@@ -1,12 +1,19 @@
-// Schedule autotuner: times candidate fg_opts for one query kind on a sample
-// batch and keeps the fastest. The window of FG_SCHED_PRIORITY is the knob
-// that matters most and its best value differs by orders of magnitude between
-// graph families (a few weight units on a low-diameter R-MAT graph, ten mean
-// weights on a road-like grid), so candidates are scaled by the graph's mean
-// arc weight (SSSP) or counted in levels (BFS) and tried from the widest
-// window down until one takes more than twice the best time; then yield
-// heuristic 2 (delta = half and a quarter of the window) is tried on top. On
-// graphs with out-degree <= 8 the lane-per-vertex expansion is tried last.
+// Autotuner: times candidate fg_opts for one query kind on a sample batch and
+// keeps the fastest. For SSSP and BFS it first picks the query group (one query
+// per warp, or the group engine with 16 or 32 lanes), which decides more than
+// any other knob: on graphs whose partitions are cut by nearly every arc the
+// group engine wins, on road-like graphs one query per warp does. Then:
+//   - one query per warp: the window of FG_SCHED_PRIORITY, whose best value
+//     differs by orders of magnitude between graph families (a few weight units
+//     on a low-diameter R-MAT graph, ten mean weights on a road-like grid), so
+//     candidates are scaled by the graph's mean arc weight (SSSP) or counted in
+//     levels (BFS) and tried from the widest down until one takes more than
+//     twice the best time; then yield heuristic 2 (delta = half and a quarter
+//     of the window); on graphs with out-degree <= 8 the lane-per-vertex
+//     expansion;
+//   - group engine (SSSP): a per-group window of 16 and 4 mean weights;
+//   - both: half the batch per launch (query_batch), which keeps a smaller
+//     working set.
 #include <cstring>
 #include <vector>
 
@@ -17,12 +24,12 @@ using namespace fg;
 namespace {
 
 fg_status time_batch(fg_graph *g, int kind, const int32_t *src, int32_t nq, void *dst, float *p, void *stream,
-                     const fg_opts &o, cudaEvent_t a, cudaEvent_t b, float *ms) {
+                     const fg_opts &o, float alpha, float eps, cudaEvent_t a, cudaEvent_t b, float *ms) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   CUDA_TRY(cudaEventRecord(a, s));
   fg_status st;
   if (kind == FG_QUERY_PPR)
-    st = fg_ppr_batch(g, src, nq, 0.15f, 1e-6f, p, nullptr, nullptr, stream, &o);
+    st = fg_ppr_batch(g, src, nq, alpha, eps, p, nullptr, nullptr, stream, &o);
   else if (kind == FG_QUERY_BFS)
     st = fg_bfs_batch(g, src, nq, static_cast<uint32_t *>(dst), stream, &o);
   else
@@ -39,12 +46,25 @@ fg_status time_batch(fg_graph *g, int kind, const int32_t *src, int32_t nq, void
 
 extern "C" fg_status fg_tune_opts(fg_graph *g, int32_t kind, const int32_t *src, int32_t nq, void *stream,
                                   fg_opts *best, fg_tune_report *report) {
+  return fg_tune_opts_ex(g, kind, src, nq, 0.15f, 1e-6f, stream, best, report);
+}
+
+extern "C" fg_status fg_tune_opts_ex(fg_graph *g, int32_t kind, const int32_t *src, int32_t nq, float alpha,
+                                     float eps, void *stream, fg_opts *best, fg_tune_report *report) {
   if (!g || !src || !best) return fail(FG_ERR_INVALID_ARG, "NULL argument");
   if (nq <= 0) return fail(FG_ERR_INVALID_ARG, "nq must be > 0");
   if (kind < FG_QUERY_SSSP || kind > FG_QUERY_PPR) return fail(FG_ERR_INVALID_ARG, "unknown query kind %d", kind);
+  if (kind == FG_QUERY_PPR && !(alpha > 0.f && alpha < 1.f)) return fail(FG_ERR_INVALID_ARG, "alpha must be in (0, 1)");
+  if (kind == FG_QUERY_PPR && !(eps > 0.f)) return fail(FG_ERR_INVALID_ARG, "eps must be > 0");
   int bucket = 0;
   while ((1 << bucket) < nq && bucket < 30) ++bucket;
-  const std::pair<int, int> key(kind, bucket);
+  // PPR choices are cached per (alpha, eps) as well
+  uint32_t ab = 0, eb = 0;
+  if (kind == FG_QUERY_PPR) {
+    std::memcpy(&ab, &alpha, 4);
+    std::memcpy(&eb, &eps, 4);
+  }
+  const TuneKey key{kind, bucket, ab, eb};
   {
     std::lock_guard<std::mutex> lk(g->mu);
     auto it = g->tuned.find(key);
@@ -60,9 +80,9 @@ extern "C" fg_status fg_tune_opts(fg_graph *g, int32_t kind, const int32_t *src,
   CUDA_TRY(cudaSetDevice(g->device));
   DevBuf out;
   CUDA_TRY(out.reserve(4 * (size_t)nq * (size_t)g->n));
-  cudaEvent_t ea = nullptr, eb = nullptr;
+  cudaEvent_t ea = nullptr, eb_ = nullptr;
   CUDA_TRY(cudaEventCreate(&ea));
-  CUDA_TRY(cudaEventCreate(&eb));
+  CUDA_TRY(cudaEventCreate(&eb_));
   struct Guard {
     cudaEvent_t a, b;
     DevBuf *o;
@@ -71,23 +91,57 @@ extern "C" fg_status fg_tune_opts(fg_graph *g, int32_t kind, const int32_t *src,
       cudaEventDestroy(b);
       o->release();
     }
-  } guard{ea, eb, &out};
+  } guard{ea, eb_, &out};
 
   fg_opts base;
   fg_default_opts(&base);
   float ms = 0.f;
   int tried = 0;
   // one untimed run loads the kernels and sizes the workspace
-  fg_status st = time_batch(g, kind, src, nq, out.p, out.as<float>(), stream, base, ea, eb, &ms);
+  fg_status st = time_batch(g, kind, src, nq, out.p, out.as<float>(), stream, base, alpha, eps, ea, eb_, &ms);
   if (st != FG_OK) return st;
-  st = time_batch(g, kind, src, nq, out.p, out.as<float>(), stream, base, ea, eb, &ms);
+  st = time_batch(g, kind, src, nq, out.p, out.as<float>(), stream, base, alpha, eps, ea, eb_, &ms);
   if (st != FG_OK) return st;
   ++tried;
   fg_opts pick = base;
   float pick_ms = ms;
   const float base_ms = ms;
 
-  if (kind != FG_QUERY_PPR) {  // PPR buffers are scheduled first-in first-out
+  auto try_opts = [&](const fg_opts &o) -> fg_status {
+    float t = 0.f;
+    fg_status s2 = time_batch(g, kind, src, nq, out.p, nullptr, stream, o, alpha, eps, ea, eb_, &t);
+    if (s2 != FG_OK) return s2;
+    ++tried;
+    if (t < pick_ms) {
+      pick = o;
+      pick_ms = t;
+    }
+    ms = t;
+    return FG_OK;
+  };
+  // the query group (the default resolves to 16 on cut-dominated graphs, else 1)
+  const int auto_group = (g->m > 0 && 2 * g->cut > g->m) ? 16 : 1;
+  if (kind != FG_QUERY_PPR) {
+    for (int G : {1, 16, 32}) {
+      if (G == auto_group) continue;
+      fg_opts o = base;
+      o.group = G;
+      if ((st = try_opts(o)) != FG_OK) return st;
+    }
+    if (pick.group == 0) pick.group = auto_group;
+  }
+  if (kind != FG_QUERY_PPR && pick.group > 1) {
+    // group engine: a per-group window (Delta-stepping across rounds) for SSSP
+    if (kind == FG_QUERY_SSSP && g->weighted) {
+      const fg_opts chosen = pick;
+      for (double f : {16.0, 4.0}) {
+        fg_opts o = chosen;
+        o.sched = FG_SCHED_PRIORITY;
+        o.sched_window = (uint32_t)(f * g->mean_weight + 0.5);
+        if ((st = try_opts(o)) != FG_OK) return st;
+      }
+    }
+  } else if (kind != FG_QUERY_PPR) {  // PPR buffers are scheduled first-in first-out
     std::vector<double> windows;
     if (kind == FG_QUERY_BFS || !g->weighted) {
       const double lv[] = {64, 48, 32, 24, 16, 12, 8, 4, 2};
@@ -104,7 +158,7 @@ extern "C" fg_status fg_tune_opts(fg_graph *g, int32_t kind, const int32_t *src,
       fg_opts o = base;
       o.sched = FG_SCHED_PRIORITY;
       o.sched_window = w;
-      st = time_batch(g, kind, src, nq, out.p, nullptr, stream, o, ea, eb, &ms);
+      st = time_batch(g, kind, src, nq, out.p, nullptr, stream, o, alpha, eps, ea, eb_, &ms);
       if (st != FG_OK) return st;
       ++tried;
       if (ms < pick_ms) {
@@ -122,7 +176,7 @@ extern "C" fg_status fg_tune_opts(fg_graph *g, int32_t kind, const int32_t *src,
         if (dl == 0u) continue;
         fg_opts o = pick;
         o.delta = dl;
-        st = time_batch(g, kind, src, nq, out.p, nullptr, stream, o, ea, eb, &ms);
+        st = time_batch(g, kind, src, nq, out.p, nullptr, stream, o, alpha, eps, ea, eb_, &ms);
         if (st != FG_OK) return st;
         ++tried;
         if (ms < pick_ms) {
@@ -134,7 +188,7 @@ extern "C" fg_status fg_tune_opts(fg_graph *g, int32_t kind, const int32_t *src,
     if (g->max_degree <= 8) {
       fg_opts o = pick;
       o.threads_per_vertex = 1;
-      st = time_batch(g, kind, src, nq, out.p, nullptr, stream, o, ea, eb, &ms);
+      st = time_batch(g, kind, src, nq, out.p, nullptr, stream, o, alpha, eps, ea, eb_, &ms);
       if (st != FG_OK) return st;
       ++tried;
       if (ms < pick_ms) {
@@ -142,6 +196,12 @@ extern "C" fg_status fg_tune_opts(fg_graph *g, int32_t kind, const int32_t *src,
         pick_ms = ms;
       }
     }
+  }
+  // half the batch per launch
+  if (nq >= 64) {
+    fg_opts o = pick;
+    o.query_batch = (nq / 2 + 31) / 32 * 32;
+    if ((st = try_opts(o)) != FG_OK) return st;
   }
   *best = pick;
   fg_tune_report r;

@@ -45,13 +45,14 @@ class fg_opts(ctypes.Structure):
                 ("sched_window", ctypes.c_uint32), ("delta", ctypes.c_uint32), ("bucket", ctypes.c_uint32),
                 ("yield_edges", ctypes.c_uint64), ("max_rounds", ctypes.c_uint32),
                 ("watchdog_ms", ctypes.c_uint32), ("emit_capacity", ctypes.c_uint64),
-                ("host_io", ctypes.c_int32), ("query_batch", ctypes.c_int32), ("threads_per_vertex", ctypes.c_int32)]
+                ("host_io", ctypes.c_int32), ("query_batch", ctypes.c_int32), ("threads_per_vertex", ctypes.c_int32),
+                ("group", ctypes.c_int32)]
 
 
 class fg_stats_t(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in
                 ("rounds", "visits", "edges", "ops", "spills", "yields", "launches", "max_round_ops")] + [
-                   ("phase_ns", ctypes.c_uint64 * 6)]
+                   ("phase_ns", ctypes.c_uint64 * 6), ("arcs_read", ctypes.c_uint64), ("group", ctypes.c_uint64)]
 
     PHASES = ("init_tiles", "seed", "scan_a", "scan_b", "scatter", "process")
 
@@ -95,8 +96,8 @@ EXPORTS = ("fg_default_opts", "fg_default_graph_opts", "fg_graph_create", "fg_gr
            "fg_graph_destroy", "fg_graph_info", "fg_sssp_batch", "fg_bfs_batch", "fg_ppr_batch", "fg_sync",
            "fg_last_error", "fg_stats", "fg_partition_plan", "fg_sssp_batch_noalloc", "fg_default_server_opts",
            "fg_server_create", "fg_server_destroy", "fg_server_submit", "fg_server_poll", "fg_server_info",
-           "fg_server_release", "fg_tune_opts", "fg_ncp_sweep", "fg_ll_build_labels", "fg_ll_query",
-           "fg_bc_accumulate", "fg_rw_batch", "fg_dfs_batch", "fg_ppr_local_batch")
+           "fg_server_release", "fg_tune_opts", "fg_tune_opts_ex", "fg_ncp_sweep", "fg_ll_build_labels",
+           "fg_ll_query", "fg_bc_accumulate", "fg_rw_batch", "fg_dfs_batch", "fg_ppr_local_batch")
 
 FG_NOALLOC_MAX_VERTICES = 1 << 20
 FG_NCP_MAX_TOP = 4096
@@ -140,6 +141,8 @@ def load():
     lib.fg_dfs_batch.argtypes = [vp, vp, i32, vp, vp]
     lib.fg_ppr_local_batch.argtypes = [vp, vp, i32, f32, f32, i32, vp, vp, vp, vp, vp]
     lib.fg_tune_opts.argtypes = [vp, i32, vp, i32, vp, ctypes.POINTER(fg_opts), ctypes.POINTER(fg_tune_report)]
+    lib.fg_tune_opts_ex.argtypes = [vp, i32, vp, i32, f32, f32, vp, ctypes.POINTER(fg_opts),
+                                    ctypes.POINTER(fg_tune_report)]
     u64p = ctypes.POINTER(ctypes.c_uint64)
     lib.fg_default_server_opts.argtypes = [ctypes.POINTER(fg_server_opts)]
     lib.fg_default_server_opts.restype = None
@@ -152,7 +155,8 @@ def load():
     for name in ("fg_graph_create", "fg_graph_create_ex", "fg_graph_destroy", "fg_graph_info", "fg_sssp_batch",
                  "fg_bfs_batch", "fg_ppr_batch", "fg_sync", "fg_stats", "fg_partition_plan",
                  "fg_sssp_batch_noalloc", "fg_server_create", "fg_server_destroy", "fg_server_submit",
-                 "fg_server_poll", "fg_server_info", "fg_server_release", "fg_tune_opts", "fg_ncp_sweep", "fg_ll_build_labels", "fg_ll_query"):
+                 "fg_server_poll", "fg_server_info", "fg_server_release", "fg_tune_opts", "fg_tune_opts_ex",
+                 "fg_ncp_sweep", "fg_ll_build_labels", "fg_ll_query"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -363,4 +367,13 @@ def fg_tune_opts(g, kind, src, nq, stream=None):
     best = fg_opts()
     rep = fg_tune_report()
     st = load().fg_tune_opts(g, kind, _ptr(src), nq, _stream(stream), ctypes.byref(best), ctypes.byref(rep))
+    return st, best, rep
+
+
+def fg_tune_opts_ex(g, kind, src, nq, alpha, eps, stream=None):
+    """As fg_tune_opts, timing PPR candidates at the caller's alpha and eps."""
+    best = fg_opts()
+    rep = fg_tune_report()
+    st = load().fg_tune_opts_ex(g, kind, _ptr(src), nq, alpha, eps, _stream(stream), ctypes.byref(best),
+                                ctypes.byref(rep))
     return st, best, rep

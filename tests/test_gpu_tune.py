@@ -62,3 +62,46 @@ def test_ppr_keeps_the_default_schedule():
         assert rep.candidates == 1 and best.sched == fg.FG_SCHED_FIFO and best.sched_window == 0
     finally:
         fg.fg_graph_destroy(h)
+
+
+def test_tuner_resolves_the_group_and_keeps_results_exact():
+    """The tuner's group, window and batch-split choices change the work, not the distances."""
+    g = inputs.rmat(12, 16, seed=13, weights=(1, 255))
+    st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, fg.fg_default_graph_opts())
+    fg.check(st)
+    try:
+        srcs = inputs.sources_uniform(g, 96, seed=8)
+        s_d = torch.from_numpy(srcs).to(DEV)
+        st, best, rep = fg.fg_tune_opts(h, fg.FG_QUERY_SSSP, s_d, len(srcs))
+        fg.check(st)
+        assert best.group in (1, 16, 32)
+        assert rep.candidates >= 4  # default, two other groups, and half the batch at least
+        out = torch.empty((len(srcs), g.n), dtype=torch.int32, device=DEV)
+        fg.check(fg.fg_sssp_batch(h, s_d, len(srcs), out, None, best))
+        fg.check(fg.fg_sync())
+        assert np.array_equal(out.cpu().numpy().view(np.uint32)[[0, 95]], oracle.sssp(g, srcs[[0, 95]]))
+        _, stats = fg.fg_stats(h)
+        assert stats.group == best.group
+    finally:
+        fg.fg_graph_destroy(h)
+
+
+def test_ppr_tuning_takes_the_callers_alpha_and_eps():
+    g = inputs.rmat(10, 8, seed=4)
+    st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, fg.fg_default_graph_opts())
+    fg.check(st)
+    try:
+        s_d = torch.from_numpy(inputs.sources_uniform(g, 16, seed=5)).to(DEV)
+        st, a, ra = fg.fg_tune_opts_ex(h, fg.FG_QUERY_PPR, s_d, 16, 0.15, 1e-7)
+        fg.check(st)
+        assert ra.candidates == 1
+        # another (alpha, eps) is timed again, not served from the cache of the first
+        st, b, rb = fg.fg_tune_opts_ex(h, fg.FG_QUERY_PPR, s_d, 16, 0.2, 1e-5)
+        fg.check(st)
+        assert rb.candidates == 1
+        st, c, rc = fg.fg_tune_opts_ex(h, fg.FG_QUERY_PPR, s_d, 16, 0.15, 1e-7)
+        fg.check(st)
+        assert rc.candidates == 0  # cached
+        assert fg.fg_tune_opts_ex(h, fg.FG_QUERY_PPR, s_d, 16, 1.5, 1e-7)[0] == fg.FG_ERR_INVALID_ARG
+    finally:
+        fg.fg_graph_destroy(h)
