@@ -1,15 +1,21 @@
 #!/usr/bin/env python3
-"""Benchmark: batched BFS + SSSP source queries on a road-like 1024x1024 grid.
+"""Benchmark: large-batch SSSP source queries on R-MAT scale 24 (the largest workload).
 
-One step = one fg_bfs_batch and one fg_sssp_batch over the same 1,024 seeded
-sources (2,048 source queries), followed by fg_sync. Three seeded source sets
-rotate across steps. Prints ONE JSON line (rank 0).
+One step = one fg_sssp_batch of B seeded sources (default 256) drawn in turn
+from the workload's 16,384 sources, on the undirected R-MAT scale-24 graph
+(16,777,216 vertices, 520,758,442 arcs, weights in [1, 255]), followed by
+fg_sync. Prints ONE JSON line (rank 0) with the device-timed rate, the
+end-to-end rate through the C ABI with host buffers, the roofline of the
+engine kernel, the CPU oracle as a reported baseline, and extra keys: the
+road-like grid workload (1,024 BFS + SSSP sources), the PPR error against the
+FP64 oracle on R-MAT scale 22, and the plain per-query GPU form.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fg|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fg|reference] [--nq B]
+    python bench.py --grid          # the grid BFS + SSSP workload as the main line
 
-Under torchrun (N > 1) every rank runs its own 1,024-source batches on its own
-GPU (weak scaling; queries are independent, so nothing is exchanged), and the
-slowest rank's time sets the whole-job rate.
+Under torchrun (N > 1) every rank runs its own batches of the 16,384 sources
+on its own GPU (weak scaling; queries are independent, so nothing is
+exchanged), and the slowest rank's time sets the whole-job rate.
 """
 from __future__ import annotations
 
@@ -29,14 +35,21 @@ import numpy as np
 ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
-WORKLOAD = "grid1024_bfs_sssp"
-GRAPH_DESC = ("road-like 2D grid 1024x1024 (1,048,576 vertices), 4-neighbour edges with 5% dropped, "
-              "1% diagonal shortcuts, int32 weights uniform in [100,10000]")
-NQ = 1024
+WORKLOAD = "rmat24_sssp"
+GRAPH_DESC = ("undirected R-MAT scale 24 (16,777,216 vertices, edge factor 16, a/b/c/d = 0.57/0.19/0.19/0.05, "
+              "self-loops and duplicates removed, 520,758,442 arcs), int32 weights uniform in [1,255]")
+WORKLOAD_SOURCES = 16384
+NQ_STEP = 256
 METRIC = "source-queries/s"
 UNIT = "queries/s"
+
+# the road-like grid workload (an extra key of the main line, or the main line with --grid)
+GRID_WORKLOAD = "grid1024_bfs_sssp"
+GRID_DESC = ("road-like 2D grid 1024x1024 (1,048,576 vertices), 4-neighbour edges with 5% dropped, "
+             "1% diagonal shortcuts, int32 weights uniform in [100,10000]")
+GRID_NQ = 1024
 SOURCE_SETS = 3
-# Scheduling for this workload (per-query priority windows, i.e. Delta-stepping
+# Scheduling for the grid workload (per-query priority windows, i.e. Delta-stepping
 # across partitions; chosen by the sweep recorded in the design notes)
 TUNED_BFS = {"sched": 1, "sched_window": 24}
 TUNED_SSSP = {"sched": 1, "sched_window": 50000}
@@ -48,7 +61,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fg", choices=["fg", "reference"])
-    ap.add_argument("--nq", type=int, default=NQ, help="sources per batch (1,024 for the workload)")
+    ap.add_argument("--nq", type=int, default=0,
+                    help="sources per step (default: 256 on R-MAT s24, 1,024 on the grid)")
+    ap.add_argument("--grid", action="store_true", help="the grid BFS + SSSP workload as the main line")
+    ap.add_argument("--graph-scale", type=int, default=0,
+                    help="plumbing tests only: a smaller R-MAT of the same recipe instead of scale 24")
+    ap.add_argument("--no-ppr-check", action="store_true", help="skip the R-MAT s22 PPR error record")
+    ap.add_argument("--no-grid-extra", action="store_true", help="skip the grid workload extra key")
+    ap.add_argument("--cpu-sources", type=int, default=0,
+                    help="sources of the CPU oracle sample (default: one per host core, at most 16)")
     ap.add_argument("--opts-bfs", default="", help="JSON overrides of fg_opts for the BFS batches")
     ap.add_argument("--opts-sssp", default="", help="JSON overrides of fg_opts for the SSSP batches")
     ap.add_argument("--partition-vertices", type=int, default=0)
@@ -78,7 +99,7 @@ def parse():
     ap.add_argument("--ll", action="store_true",
                     help="only the LL application: 1,024 SSSPs on the grid, labels, 2^20 distance queries")
     ap.add_argument("--ll-pairs", type=int, default=1 << 20, help="pairs per query batch of the LL run")
-    ap.add_argument("--ll-landmarks", type=int, default=NQ, help="landmarks of the LL run (1,024 = the workload)")
+    ap.add_argument("--ll-landmarks", type=int, default=GRID_NQ, help="landmarks of the LL run (1,024 = the workload)")
     ap.add_argument("--ablation", action="store_true",
                     help="only the scheduling / yield / partition-size ablation on the bench workload")
     return ap.parse_args()
@@ -108,9 +129,37 @@ def job_rate(queries_per_rank: int, world_size: int, slowest_ms: float) -> float
     return queries_per_rank * world_size / (slowest_ms / 1000.0)
 
 
-def source_sets(g, rank, nq=NQ):
+def source_sets(g, rank, nq=GRID_NQ):
+    """The grid workload's seeded source sets of one rank (each rank draws its own)."""
     from paper_2103_14915_gb300 import inputs
-    return [inputs.workload_sources(WORKLOAD, g, NQ, set_index=100 * rank + i)[:nq] for i in range(SOURCE_SETS)]
+    return [inputs.workload_sources(GRID_WORKLOAD, g, GRID_NQ, set_index=100 * rank + i)[:nq]
+            for i in range(SOURCE_SETS)]
+
+
+def step_sources(all_srcs: np.ndarray, rank: int, world: int, step: int, nb: int) -> np.ndarray:
+    """Sources of one step of one rank: block (step * world + rank) of nb consecutive
+    sources of the workload's list, wrapping around. Within a step the ranks take
+    different blocks, so the job covers the list once before any source repeats."""
+    blocks = max(1, len(all_srcs) // nb)
+    b = (step * world + rank) % blocks
+    return np.ascontiguousarray(all_srcs[b * nb:(b + 1) * nb])
+
+
+def csr_sha256_check(g, name):
+    """(computed, recorded, match) for a workload graph, against tests/golden/csr_sha256.txt."""
+    h = hashlib.sha256()
+    h.update(g.row_ptr.astype("<i8", copy=False).tobytes())
+    h.update(g.col.astype("<i4", copy=False).tobytes())
+    if g.w is not None:
+        h.update(g.w.astype("<i4", copy=False).tobytes())
+    got = h.hexdigest()
+    rec = None
+    f = ROOT / "tests" / "golden" / "csr_sha256.txt"
+    if f.exists():
+        for ln in f.read_text().splitlines():
+            if ln.startswith(name + " "):
+                rec = dict(x.split("=", 1) for x in ln.split()[1:]).get("csr")
+    return got, rec, got == rec
 
 
 class ClockSampler:
@@ -257,14 +306,55 @@ def serve_stream(fg, h, g, lam, n_req, seed, lanes, max_batch, kinds=(0, 1, 2), 
             "mean_batch": float(np.mean(batch)), "lanes": lanes, "max_batch": max_batch}
 
 
+def bench_graph(args):
+    """The bench graph: the R-MAT scale-24 workload, or (for plumbing tests only) a
+    smaller R-MAT of the same recipe with --graph-scale."""
+    from paper_2103_14915_gb300 import inputs
+    if args.graph_scale:
+        g = inputs.rmat(args.graph_scale, 16, seed=args.graph_scale, weights=(1, 255))
+        return g, f"rmat{args.graph_scale}_sssp", f"undirected R-MAT scale {args.graph_scale} (test size)"
+    return inputs.workload_graph(WORKLOAD), WORKLOAD, GRAPH_DESC
+
+
 def run_reference(args):
-    """The oracle (CPU, OpenMP over queries) on a bounded sample of the same workload."""
+    """The oracle (CPU: binary-heap Dijkstra, OpenMP over queries, one per host core) on a
+    bounded sample of the bench workload: each step runs one source per host core (at
+    most 16) from the workload's source list, in turn."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle
     from paper_2103_14915_gb300 import inputs
-    g = inputs.workload_graph(WORKLOAD)
+    if args.grid:
+        return run_reference_grid(args)
+    g, name, desc = bench_graph(args)
+    all_srcs = inputs.workload_sources(WORKLOAD, g) if not args.graph_scale else inputs.sources_uniform(
+        g, int((np.diff(g.row_ptr) > 0).sum()) // 2, 1)
+    cores = oracle.num_threads()
+    per_step = args.cpu_sources or max(1, min(cores, 16))
+    for i in range(args.warmup):
+        oracle.sssp(g, step_sources(all_srcs, 0, 1, i, per_step))
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle.sssp(g, step_sources(all_srcs, 0, 1, args.warmup + i, per_step))
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    sample = f"{per_step} sources per step of the {len(all_srcs):,}-source list, {args.steps} steps"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": name, "graph": desc, "queries_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_reference_grid(args):
+    """The oracle on a bounded sample of the grid workload (32 sources per step, BFS + SSSP)."""
+    import oracle
+    from paper_2103_14915_gb300 import inputs
+    g = inputs.workload_graph(GRID_WORKLOAD)
     sets = source_sets(g, 0)
     per_step = 32
     cores = oracle.num_threads()
@@ -284,7 +374,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "graph": GRAPH_DESC, "queries_per_step": 2 * per_step},
+        "config": {"workload": GRID_WORKLOAD, "graph": GRID_DESC, "queries_per_step": 2 * per_step},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -337,8 +427,8 @@ def run_ablation(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2103_14915_gb300 import fg, inputs
-    g = inputs.workload_graph(WORKLOAD)
-    nq = args.nq
+    g = inputs.workload_graph(GRID_WORKLOAD)
+    nq = args.nq or GRID_NQ
     src = torch.from_numpy(source_sets(g, 0, nq)[0]).to(dev)
     mu_arcs = None
     rows = []
@@ -394,7 +484,7 @@ def run_ablation(args):
             rows.append(row)
             print(json.dumps(row), file=sys.stderr, flush=True)
         fg.fg_graph_destroy(h)
-    print(json.dumps({"metric": "ablation", "workload": WORKLOAD, "sources": nq, "rows": rows}), flush=True)
+    print(json.dumps({"metric": "ablation", "workload": GRID_WORKLOAD, "sources": nq, "rows": rows}), flush=True)
 
 
 def run_ncp(args):
@@ -718,8 +808,8 @@ def run_ll(args):
     __graft_entry__.build()
     import oracle
     from paper_2103_14915_gb300 import fg, inputs
-    g = inputs.workload_graph(WORKLOAD)
-    lms = inputs.workload_sources(WORKLOAD, g, k=args.ll_landmarks)
+    g = inputs.workload_graph(GRID_WORKLOAD)
+    lms = inputs.workload_sources(GRID_WORKLOAD, g, k=args.ll_landmarks)
     K, n, Q = len(lms), g.n, args.ll_pairs
     gopts = fg.fg_default_graph_opts(partition_method=fg.FG_PART_GROW, partition_vertices=args.partition_vertices)
     st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, gopts)
@@ -916,35 +1006,310 @@ def run_configs(args):
     print(json.dumps(res), flush=True)
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        run_reference(args)
-        return
-    if args.serving:
-        run_serving(args)
-        return
-    if args.ablation:
-        run_ablation(args)
-        return
-    if args.ncp:
-        run_ncp(args)
-        return
-    if args.ll:
-        run_ll(args)
-        return
-    if args.bc:
-        run_bc(args)
-        return
-    if args.walks:
-        run_walks(args)
-        return
-    if args.local_ppr:
-        run_local_ppr(args)
-        return
-    if args.configs:
-        run_configs(args)
-        return
+def kernel_traffic(profile: str, source: str):
+    """DRAM bytes per launch from a committed ncu summary, while the kernel source it
+    was taken from is unchanged (else None)."""
+    src = (ROOT / "paper_2103_14915_gb300" / "csrc" / source).read_bytes()
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    f = ROOT / "profiles" / profile
+    if not f.exists():
+        return None
+    kv = {}
+    for ln in f.read_text().splitlines():
+        if ":" in ln and not ln.startswith("#"):
+            k, v = ln.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_sha256_16") != sha:
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def ppr_error_record(fg, inputs, oracle, dev, k=8):
+    """PPR forward push on R-MAT s22 (alpha 0.15, eps 1e-7), all 4,096 log-degree seeds, against
+    the FP64 power iteration (to 1e-12) on k seeds spread over the log2-degree buckets, the
+    top (hub) bucket included: max / mean / p99 over vertices of |p - pi| / (eps * d)."""
+    import torch
+    alpha, eps = 0.15, 1e-7
+    g = inputs.workload_graph("rmat22_ppr")
+    srcs = inputs.workload_sources("rmat22_ppr", g)
+    st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, fg.fg_default_graph_opts())
+    fg.check(st)
+    try:
+        nq = len(srcs)
+        s_d = torch.from_numpy(srcs).to(dev)
+        p = torch.empty((nq, g.n), dtype=torch.float32, device=dev)
+        mass = torch.empty(nq, dtype=torch.float64, device=dev)
+        t0 = time.perf_counter()
+        fg.check(fg.fg_ppr_batch(h, s_d, nq, alpha, eps, p, None, mass, None, fg.fg_default_opts()))
+        fg.check(fg.fg_sync())
+        t_gpu = time.perf_counter() - t0
+        deg = np.diff(g.row_ptr).astype(np.float64)
+        order = np.argsort(deg[srcs], kind="stable")
+        rows = [int(order[i]) for i in np.unique(np.round(np.linspace(0, nq - 1, k)).astype(np.int64))]
+        t0 = time.perf_counter()
+        pi = oracle.ppr_power(g, srcs[rows], alpha)
+        t_cpu = time.perf_counter() - t0
+        got = p[torch.as_tensor(rows, device=dev)].cpu().numpy().astype(np.float64)
+        ratio = np.abs(got - pi) / (eps * np.maximum(deg, 1.0))
+        within = bool(np.all(np.abs(got - pi) <= eps * deg + 1e-6))
+        return {"workload": "rmat22_ppr", "alpha": alpha, "eps": eps, "seeds": nq, "checked_seeds": len(rows),
+                "checked_seed_degrees": [int(deg[srcs[r]]) for r in rows],
+                "max_err_over_eps_deg": float(ratio.max()), "mean_err_over_eps_deg": float(ratio.mean()),
+                "p99_err_over_eps_deg": float(np.percentile(ratio, 99)), "within_bound": within,
+                "mass_err_max": float((mass - 1.0).abs().max()), "batch_s": t_gpu, "oracle_s": t_cpu,
+                "bound": "|p - pi| <= eps * d + 1e-6 per vertex (undirected)"}
+    finally:
+        fg.fg_graph_destroy(h)
+
+
+def grid_extra(fg, inputs, dev, stream):
+    """The grid workload (1,024 BFS + 1,024 SSSP sources, one batch each, hand-swept schedules)."""
+    import torch
+    g = inputs.workload_graph(GRID_WORKLOAD)
+    srcs = source_sets(g, 0)[0]
+    st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0,
+                                  fg.fg_default_graph_opts(partition_method=fg.FG_PART_GROW))
+    fg.check(st)
+    try:
+        s_d = torch.from_numpy(srcs).to(dev)
+        out = torch.empty((GRID_NQ, g.n), dtype=torch.int32, device=dev)
+        res = {}
+        for kind, opts in (("bfs", TUNED_BFS), ("sssp", TUNED_SSSP)):
+            f = fg.fg_bfs_batch if kind == "bfs" else fg.fg_sssp_batch
+            o = fg.fg_default_opts(**opts)
+            fg.check(f(h, s_d, GRID_NQ, out, stream, o))
+            fg.check(fg.fg_sync(stream))
+            ms = []
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fg.check(f(h, s_d, GRID_NQ, out, stream, o))
+                b.record(stream)
+                fg.check(fg.fg_sync(stream))
+                ms.append(a.elapsed_time(b))
+            d = fg.fg_stats(h)[1].as_dict()
+            res[kind] = {"ms": statistics.median(ms), "opts": opts, "group": d["group"], "rounds": d["rounds"]}
+        res["value"] = 2 * GRID_NQ / ((res["bfs"]["ms"] + res["sssp"]["ms"]) / 1e3)
+        res["unit"] = UNIT
+        res["graph"] = GRID_DESC
+        return res
+    finally:
+        fg.fg_graph_destroy(h)
+
+
+def run_rmat24(args):
+    """The main line: SSSP batches of B sources on R-MAT scale 24 (see the module docstring)."""
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if ws > 1:
+        dist.barrier()
+        __graft_entry__.build()
+    from paper_2103_14915_gb300 import fg, inputs
+
+    t0 = time.perf_counter()
+    g, name, desc = bench_graph(args)
+    gen_s = time.perf_counter() - t0
+    sha_got, sha_rec, sha_ok = csr_sha256_check(g, name)
+    all_srcs = inputs.workload_sources(WORKLOAD, g) if not args.graph_scale else inputs.sources_uniform(
+        g, int((np.diff(g.row_ptr) > 0).sum()) // 2, 1)
+    nb = args.nq or NQ_STEP
+    t0 = time.perf_counter()
+    st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, fg.fg_default_graph_opts())
+    fg.check(st)
+    create_s = time.perf_counter() - t0
+    st, info = fg.fg_graph_info(h)
+    fg.check(st)
+    stream = torch.cuda.current_stream(dev)
+    # schedule and query group: the library's autotuner on a 64-source sample taken
+    # apart from the timed sources (outside the timed region)
+    keys = ("group", "sched", "sched_window", "delta", "threads_per_vertex")
+    if args.no_tune:
+        opts_d = {}
+        tune = {"chosen_by": "defaults (--no-tune)"}
+    else:
+        sample = torch.from_numpy(inputs.sources_uniform(g, 64, 4242)).to(dev)
+        t0 = time.perf_counter()
+        st, best, rep = fg.fg_tune_opts(h, fg.FG_QUERY_SSSP, sample, 64, stream)
+        fg.check(st)
+        opts_d = {k: int(getattr(best, k)) for k in keys}
+        tune = {"chosen_by": "fg_tune_opts on 64 sources outside the timed set", "candidates": rep.candidates,
+                "best_ms": rep.best_ms, "default_ms": rep.default_ms, "tune_s": time.perf_counter() - t0}
+    opts_d.update(json.loads(args.opts_sssp) if args.opts_sssp else {})
+    opts = fg.fg_default_opts(**opts_d)
+    out = torch.empty((nb, g.n), dtype=torch.int32, device=dev)
+    n_steps = args.warmup + args.steps
+    src_d = [torch.from_numpy(step_sources(all_srcs, rank, ws, i, nb)).to(dev) for i in range(n_steps)]
+
+    def step(i, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        fg.check(fg.fg_sssp_batch(h, src_d[i], nb, out, stream, opts))
+        if ev is not None:
+            ev[1].record(stream)
+        fg.check(fg.fg_sync(stream))
+
+    for i in range(args.warmup):
+        step(i)
+    st, stats = fg.fg_stats(h)
+    fg.check(st)
+    launches_per_step = int(stats.launches)
+
+    clocks = ClockSampler(local)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_stats = []
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    t_start.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i, evs[i])
+        step_stats.append(fg.fg_stats(h)[1].as_dict())
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    elapsed_ms = max_over_ranks(t_start.elapsed_time(t_end), dev)
+    value = job_rate(nb * args.steps, ws, elapsed_ms)
+    batch_ms = [e[0].elapsed_time(e[1]) for e in evs]
+
+    # GTEPS: arcs out of the vertices each query reaches (what a sequential Dijkstra scans), last step
+    deg = torch.from_numpy(np.diff(g.row_ptr).astype(np.int64)).to(dev)
+    reach_arcs = int(((out != -1).to(torch.int64) * deg[None, :]).sum().item())
+    arcs_per_query = reach_arcs / nb
+    gteps = arcs_per_query * value / 1e9
+
+    # roofline of the engine launch (algorithmic bytes per launch / CUDA-event time per batch)
+    peak, peak_kind = measured_peaks()
+    mean = lambda k: statistics.mean(float(d[k]) for d in step_stats)
+    group = int(step_stats[-1]["group"])
+    out_bytes = 4 * g.n * nb
+    arc_bytes = 8 * mean("arcs_read")
+    op_bytes = 16 * mean("ops")
+    alg_bytes = out_bytes + arc_bytes + op_bytes
+    kern_ms = statistics.mean(batch_ms)
+    achieved = alg_bytes / (kern_ms / 1000.0) / 1e9
+    kernel = "fg::group_kernel<0>" if group > 1 else "fg::engine_kernel<0>"
+    traffic = kernel_traffic("group_kernel_rmat24_traffic.txt", "fg_group.cu") if group > 1 else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": f"{peak_kind} hbm_gbs (STREAM-style copy)", "kernel": kernel,
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "algorithmic_terms": {"output_4B_per_vertex_query": out_bytes, "arcs_8B_per_arc_read": arc_bytes,
+                                      "operations_16B_each": op_bytes},
+                "batch_ms": kern_ms, "timing": "CUDA events around each fg_sssp_batch on its stream "
+                                               "(engine launch + its output transpose)"}
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": name, "graph": desc, "sources_per_step": nb, "kinds": ["sssp"],
+                   "workload_sources": len(all_srcs),
+                   "sources_timed": nb * args.steps * ws,
+                   "fraction_of_workload_timed": min(1.0, nb * args.steps * ws / len(all_srcs)),
+                   "partition": {"method": int(info.partition_method), "S": int(info.partition_vertices),
+                                 "parts": int(info.num_partitions), "cut_arcs": int(info.cut_arcs)},
+                   "opts": opts_d, "tuner": tune,
+                   "l2": f"inputs larger than L2: each step writes {4 * nb * g.n / 1e9:.1f} GB of distances "
+                         f"and the query state is {8 * nb * g.n / 1e9:.1f} GB",
+                   "parallelism": f"queries sharded over {ws} GPU(s)"},
+        "gteps": gteps, "arcs_per_query_dijkstra": arcs_per_query,
+        "roofline": roofline,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "stats": step_stats[-1],
+        "graph_build": {"generate_s": gen_s, "create_s": create_s, "csr_sha256": sha_got,
+                        "csr_sha256_recorded": sha_rec, "csr_sha256_ok": sha_ok},
+    }
+
+    if not args.no_extras:
+        # end to end through the C ABI with host buffers: every step copies its sources in
+        # from pinned host memory and every distance row out to pinned host memory, with
+        # asynchronous host I/O (host_io = 2) on two streams, so one batch's copy-out runs
+        # behind the next batch's kernels
+        o_h = fg.fg_default_opts(**opts_d)
+        o_h.host_io = 2
+        outs_h = [torch.empty((nb, g.n), dtype=torch.int32, pin_memory=True) for _ in range(2)]
+        srcs_h = [torch.from_numpy(step_sources(all_srcs, rank, ws, i, nb)).pin_memory() for i in range(n_steps)]
+        streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+        fg.check(fg.fg_sssp_batch(h, srcs_h[0].data_ptr(), nb, outs_h[0].data_ptr(), streams[0], o_h))
+        fg.check(fg.fg_sync(streams[0]))
+        e_steps = args.steps
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for i in range(e_steps):
+            k = i & 1
+            if i >= 2:
+                fg.check(fg.fg_sync(streams[k]))  # this host buffer's previous batch is complete
+            fg.check(fg.fg_sssp_batch(h, srcs_h[args.warmup + i].data_ptr(), nb, outs_h[k].data_ptr(),
+                                      streams[k], o_h))
+        for k in range(2):
+            fg.check(fg.fg_sync(streams[k]))
+        e_dt = time.perf_counter() - t0
+        e_value = max_over_ranks(e_dt * 1000.0, dev)
+        result["e2e"] = {"value": job_rate(nb * e_steps, ws, e_value), "unit": UNIT,
+                         "h2d_bytes_per_step": 4 * nb, "d2h_bytes_per_step": 4 * nb * g.n, "steps": e_steps,
+                         "api": "fg_sssp_batch with host_io=2 (pinned host buffers, two streams)"}
+        del outs_h
+        if rank == 0:
+            import oracle
+            # the plain per-query GPU form on a sample of the same sources
+            k = max(1, args.plain_sample // 4)
+            o_plain = fg.fg_default_opts(mode=fg.FG_MODE_PLAIN)
+            s = src_d[0][:k].contiguous()
+            fg.check(fg.fg_sssp_batch(h, s, 1, out, stream, o_plain))
+            fg.check(fg.fg_sync(stream))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fg.check(fg.fg_sssp_batch(h, s, k, out, stream, o_plain))
+            b.record(stream)
+            fg.check(fg.fg_sync(stream))
+            result["plain_gpu"] = {"value": k / (a.elapsed_time(b) / 1000.0), "unit": UNIT,
+                                   "sample": f"{k} sources, one query at a time (FG_MODE_PLAIN)"}
+            # parity of the timed path on a sampled row, and the CPU oracle on the host cores
+            cores = oracle.num_threads()
+            kc = args.cpu_sources or max(1, min(cores, 16))
+            cs = step_sources(all_srcs, 0, 1, 0, kc)
+            t0 = time.perf_counter()
+            ref = oracle.sssp(g, cs)
+            cdt = time.perf_counter() - t0
+            fg.check(fg.fg_sssp_batch(h, torch.from_numpy(cs).to(dev), kc, out, stream, opts))
+            fg.check(fg.fg_sync(stream))
+            result["exact_sampled"] = {"rows": kc, "exact": bool(np.array_equal(
+                out[:kc].cpu().numpy().view(np.uint32), ref))}
+            result["cpu_baseline"] = {"value": kc / cdt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                      "sample": f"{kc} of the {len(all_srcs):,} sources (one per host core), "
+                                                "binary-heap Dijkstra, OpenMP over queries"}
+            fg.fg_graph_destroy(h)
+            h = None
+            del out
+            torch.cuda.empty_cache()
+            if not args.no_grid_extra:
+                result["grid1024_bfs_sssp"] = grid_extra(fg, inputs, dev, stream)
+            if not args.no_ppr_check:
+                result["ppr_rmat22"] = ppr_error_record(fg, inputs, oracle, dev)
+    if h is not None:
+        fg.fg_graph_destroy(h)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def run_grid(args):
+    """The grid workload as the main line: one step = one BFS and one SSSP batch of the same
+    1,024 seeded sources (2,048 source queries); three source sets rotate across steps."""
     import torch
     ws, rank, local = dist_env()
     if ws > 1:
@@ -961,8 +1326,8 @@ def main():
         __graft_entry__.build()
     from paper_2103_14915_gb300 import fg, inputs
 
-    g = inputs.workload_graph(WORKLOAD)
-    nq = args.nq
+    g = inputs.workload_graph(GRID_WORKLOAD)
+    nq = args.nq or GRID_NQ
     sets = source_sets(g, rank, nq)
     gopts = fg.fg_default_graph_opts(partition_method=fg.FG_PART_GROW, partition_vertices=args.partition_vertices)
     st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, gopts)
@@ -1062,7 +1427,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "graph": GRAPH_DESC, "sources_per_batch": nq, "kinds": ["bfs", "sssp"],
+        "config": {"workload": GRID_WORKLOAD, "graph": GRID_DESC, "sources_per_batch": nq, "kinds": ["bfs", "sssp"],
                    "queries_per_step": 2 * nq, "source_sets": SOURCE_SETS,
                    "partition": {"method": "grow", "S": int(info.partition_vertices),
                                  "parts": int(info.num_partitions), "cut_arcs": int(info.cut_arcs)},
@@ -1138,12 +1503,49 @@ def main():
             result["serving"] = dict(
                 serve_stream(fg, h, g, args.serve_lambda, args.serve_requests, seed=77, lanes=4, max_batch=128,
                              kinds=(0, 1, 2), alpha=0.15, eps=1e-6, opts={0: extra_s, 1: extra_b}),
-                graph=WORKLOAD, mix="1/3 SSSP, 1/3 BFS, 1/3 PPR(alpha=0.15, eps=1e-6)")
+                graph=GRID_WORKLOAD, mix="1/3 SSSP, 1/3 BFS, 1/3 PPR(alpha=0.15, eps=1e-6)")
     fg.fg_graph_destroy(h)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    if args.serving:
+        run_serving(args)
+        return
+    if args.ablation:
+        run_ablation(args)
+        return
+    if args.ncp:
+        run_ncp(args)
+        return
+    if args.ll:
+        run_ll(args)
+        return
+    if args.bc:
+        run_bc(args)
+        return
+    if args.walks:
+        run_walks(args)
+        return
+    if args.local_ppr:
+        run_local_ppr(args)
+        return
+    if args.configs:
+        run_configs(args)
+        return
+    if args.grid:
+        run_grid(args)
+        return
+    run_rmat24(args)
 
 
 if __name__ == "__main__":

@@ -15,8 +15,10 @@ ROOT = Path(__file__).resolve().parents[1]
 
 
 def test_reference_arm_line():
+    # a scale-12 R-MAT of the bench recipe keeps the CPU suite short (the box runs scale 24)
     out = subprocess.run([sys.executable, str(ROOT / "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "3"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+                          "--warmup", "3", "--graph-scale", "12", "--cpu-sources", "4"], cwd=ROOT,
+                         capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [line for line in out.stdout.splitlines() if line.startswith("{")]
     assert len(lines) == 1
@@ -26,7 +28,7 @@ def test_reference_arm_line():
         assert k in d, k
     assert d["impl"] == "reference" and d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1
     assert d["value"] > 0 and d["higher_is_better"] is True and d["vs_baseline"] is None
-    assert d["config"]["workload"] == "grid1024_bfs_sssp"
+    assert d["config"]["workload"] == "rmat12_sssp" and d["config"]["queries_per_step"] == 4
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
@@ -34,7 +36,7 @@ def test_reference_arm_line():
 
 
 @pytest.mark.parametrize("flag", ["--configs", "--serving", "--ablation", "--ncp", "--ll", "--bc", "--walks",
-                                  "--local-ppr"])
+                                  "--local-ppr", "--grid"])
 def test_every_mode_flag_parses(flag, monkeypatch):
     sys.path.insert(0, str(ROOT))
     import bench
@@ -42,3 +44,19 @@ def test_every_mode_flag_parses(flag, monkeypatch):
     args = bench.parse()
     assert getattr(args, flag[2:].replace("-", "_")) is True
     assert args.gpus == 1 and args.impl == "fg"
+
+
+def test_step_sources_cover_the_list_before_repeating():
+    sys.path.insert(0, str(ROOT))
+    import numpy as np
+    import bench
+    srcs = np.arange(1000, dtype=np.int32)
+    seen = []
+    for step in range(5):
+        for rank in range(2):
+            b = bench.step_sources(srcs, rank, 2, step, 100)
+            assert len(b) == 100 and b.flags["C_CONTIGUOUS"]
+            seen.append(b)
+    allv = np.concatenate(seen)
+    assert len(np.unique(allv)) == 1000  # ten blocks of 100, each once
+    assert np.array_equal(bench.step_sources(srcs, 0, 2, 5, 100), seen[0])  # then the list wraps
