@@ -317,9 +317,11 @@ def bench_graph(args):
 
 
 def run_reference(args):
-    """The oracle (CPU: binary-heap Dijkstra, OpenMP over queries, one per host core) on a
-    bounded sample of the bench workload: each step runs one source per host core (at
-    most 16) from the workload's source list, in turn."""
+    """The oracle (CPU: binary-heap Dijkstra, OpenMP over queries, one query per host
+    core at a time: the paper's t = 1 scheme) on a bounded sample of the bench
+    workload: one source per step, the K timed steps' sources in one oracle call
+    (so they run side by side on the host cores), after the W warm-up steps' sources
+    in another."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
@@ -331,20 +333,21 @@ def run_reference(args):
     all_srcs = inputs.workload_sources(WORKLOAD, g) if not args.graph_scale else inputs.sources_uniform(
         g, int((np.diff(g.row_ptr) > 0).sum()) // 2, 1)
     cores = oracle.num_threads()
-    per_step = args.cpu_sources or max(1, min(cores, 16))
-    for i in range(args.warmup):
-        oracle.sssp(g, step_sources(all_srcs, 0, 1, i, per_step))
+    warm = step_sources(all_srcs, 0, 1, 0, max(1, args.warmup))
+    timed = step_sources(all_srcs, 0, 1, 1, max(1, args.steps)) if args.steps > 0 else warm[:0]
+    if args.warmup > 0:
+        oracle.sssp(g, warm[:args.warmup])
     t0 = time.perf_counter()
-    for i in range(args.steps):
-        oracle.sssp(g, step_sources(all_srcs, 0, 1, args.warmup + i, per_step))
+    oracle.sssp(g, timed)
     dt = time.perf_counter() - t0
-    value = per_step * args.steps / dt
-    sample = f"{per_step} sources per step of the {len(all_srcs):,}-source list, {args.steps} steps"
+    value = len(timed) / dt
+    sample = (f"one source per step ({len(timed)} timed, {args.warmup} warm-up) from the {len(all_srcs):,}-source "
+              f"list, run side by side on {cores} host cores")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": name, "graph": desc, "queries_per_step": per_step},
+        "config": {"workload": name, "graph": desc, "queries_per_step": 1},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -456,20 +459,27 @@ def run_ablation(args):
         fg.check(st)
         info = fg.fg_graph_info(h)[1]
         mu = g.m // max(1, info.num_partitions) // nq  # arcs per partition per query (yield heuristic 1 unit)
-        cfgs = [("fifo", {}, {}),
-                ("priority-window", TUNED_BFS, TUNED_SSSP)]
+        mu_exact = g.m / max(1, info.num_partitions) / nq  # mu = |E_P| / |Q| (App. A)
+        cfgs = [("fifo", {"group": 1}, {"group": 1}),
+                ("priority-window (Shortest, Tab. 4A)", TUNED_BFS, TUNED_SSSP)]
         if S == 1024 and method == fg.FG_PART_GROW:
-            cfgs += [("priority-window/2", {"sched": 1, "sched_window": TUNED_BFS["sched_window"] // 2},
+            # Tab. 4A: the four inter-partition schedulers (FIFO and Shortest above)
+            cfgs += [("max-ops (Tab. 4A)", {"sched": fg.FG_SCHED_MAXOPS}, {"sched": fg.FG_SCHED_MAXOPS}),
+                     ("random (Tab. 4A)", {"sched": fg.FG_SCHED_RANDOM}, {"sched": fg.FG_SCHED_RANDOM}),
+                     ("priority-window/2", {"sched": 1, "sched_window": TUNED_BFS["sched_window"] // 2},
                       {"sched": 1, "sched_window": TUNED_SSSP["sched_window"] // 2}),
                      ("priority-window*2", {"sched": 1, "sched_window": TUNED_BFS["sched_window"] * 2},
                       {"sched": 1, "sched_window": TUNED_SSSP["sched_window"] * 2}),
-                     ("delta-yield (heuristic 2)", {"delta": 8}, {"delta": 20000}),
-                     ("edge-budget 4*mu (heuristic 1)", dict(TUNED_BFS, yield_edges=max(1, 4 * mu)),
-                      dict(TUNED_SSSP, yield_edges=max(1, 4 * mu))),
-                     ("edge-budget 64*mu (heuristic 1)", dict(TUNED_BFS, yield_edges=max(1, 64 * mu)),
-                      dict(TUNED_SSSP, yield_edges=max(1, 64 * mu))),
-                     ("lane-per-vertex expansion", dict(TUNED_BFS, threads_per_vertex=1),
-                      dict(TUNED_SSSP, threads_per_vertex=1))]
+                     ("delta-yield (heuristic 2)", {"delta": 8}, {"delta": 20000})]
+            # Tab. 4B: edge budget (yield heuristic 1) of {0.25, 0.5, 1, 2, 4} mu on the priority window
+            for f in (0.25, 0.5, 1.0, 2.0, 4.0):
+                yb = max(1, int(round(f * mu_exact)))
+                cfgs.append((f"edge-budget {f}*mu (Tab. 4B)", dict(TUNED_BFS, yield_edges=yb),
+                             dict(TUNED_SSSP, yield_edges=yb)))
+            cfgs += [("lane-per-vertex expansion", dict(TUNED_BFS, threads_per_vertex=1),
+                      dict(TUNED_SSSP, threads_per_vertex=1)),
+                     ("group engine G=16 (lanes = queries)", {"group": 16}, {"group": 16}),
+                     ("group engine G=32 (lanes = queries)", {"group": 32}, {"group": 32})]
         for name, ob, os_ in cfgs:
             row = {"S": S, "partition": "grow" if method == fg.FG_PART_GROW else "range", "config": name,
                    "cut_arcs": int(info.cut_arcs)}

@@ -65,8 +65,8 @@ typedef struct {
     int32_t partition_vertices;  /* S, a power of two in [32, 4096]; 0 = from the on-chip budget */
 } fg_graph_opts;
 
-/* inter-partition scheduling (Sec. 5.2) */
-enum { FG_SCHED_FIFO = 0, FG_SCHED_PRIORITY = 1 };
+/* inter-partition scheduling (Sec. 5.2; the four schedulers of Tab. 4A) */
+enum { FG_SCHED_FIFO = 0, FG_SCHED_PRIORITY = 1, FG_SCHED_MAXOPS = 2, FG_SCHED_RANDOM = 3 };
 /* execution form */
 enum { FG_MODE_BUFFERED = 0, FG_MODE_PLAIN = 1 };
 
@@ -74,9 +74,16 @@ typedef struct {
     uint32_t struct_size;   /* sizeof(fg_opts); fields past it keep their defaults */
     int32_t mode;           /* FG_MODE_BUFFERED (default); FG_MODE_PLAIN runs one query at a
                                time with ordinary whole-graph frontier kernels (the baseline) */
-    int32_t sched;          /* FG_SCHED_FIFO (default, Sec. 5.2) or FG_SCHED_PRIORITY: each
-                               round processes a query's buffers whose best value lies within
-                               sched_window of that query's best pending value */
+    int32_t sched;          /* FG_SCHED_FIFO (default, Sec. 5.2): every round processes every
+                               non-empty buffer; FG_SCHED_PRIORITY ("Shortest"): a query's
+                               buffers whose best value lies within sched_window of that
+                               query's best pending value; FG_SCHED_MAXOPS: buffers holding at
+                               least a quarter of the round's largest buffer's operations;
+                               FG_SCHED_RANDOM: a seeded coin per (buffer, round). Buffers left
+                               out carry their work to the next round, where they are always
+                               taken (no starvation). SSSP/BFS with one query per warp; PPR
+                               and the group engine run FIFO rounds (the group engine with its
+                               own window, see group) */
     uint32_t sched_window;  /* window of FG_SCHED_PRIORITY (SSSP/BFS value units); 0 = 8 * delta */
     uint32_t delta;         /* yield heuristic 2 (Sec. 5.1): within one visit a query processes
                                values below (first value + delta); the rest stays buffered.

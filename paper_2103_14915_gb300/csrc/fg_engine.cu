@@ -771,6 +771,18 @@ __device__ void visit_ppr(const EngineArgs &a, const WarpSmem &w0, uint4 item, c
   store_slice(reinterpret_cast<uint32_t *>(rrow + base), w.d, Sp, lane);
 }
 
+// Coin of the random scheduler: a 32-bit mix of (key, round) (the finalizer
+// of MurmurHash3, Appleby 2011).
+__device__ __forceinline__ uint32_t sched_coin(uint32_t key, uint32_t round) {
+  uint32_t x = key * 0x9E3779B1u ^ (round + 1u) * 0x85EBCA77u;
+  x ^= x >> 16;
+  x *= 0x85EBCA6Bu;
+  x ^= x >> 13;
+  x *= 0xC2B2AE35u;
+  x ^= x >> 16;
+  return x;
+}
+
 // Buffer skipped by priority scheduling this round (SSSP/BFS). No warp stages
 // this (partition, query) slice in the current round, so its operations are
 // applied directly to the query's state with atomicMin and the improved
@@ -963,6 +975,7 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
     // ---- SCAN-A: per-block totals ----
     {
       unsigned long long loc = 0, hv = 0;
+      uint32_t mx = 0;  // largest buffer of the round (max-operations scheduling)
 #pragma unroll 4
       for (uint64_t k = k0 + threadIdx.x; k < k1; k += kThreads) {
         const uint32_t n_ops = __ldcg(a.cnt + k);
@@ -972,6 +985,11 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
         hv += dk ? 1ull : 0ull;
         if (!kPPR && act && a.sched == FG_SCHED_PRIORITY)
           atomicMin(&qb_cur[(uint32_t)k % (uint32_t)a.nq], __ldcg(a.prio + k));
+        if (!kPPR && a.sched == FG_SCHED_MAXOPS) mx = n_ops > mx ? n_ops : mx;
+      }
+      if (!kPPR && a.sched == FG_SCHED_MAXOPS) {
+        mx = __reduce_max_sync(kFull, mx);
+        if (lane == 0 && mx > 0u) atomicMax(&c->max_ops[round & 1u], mx);
       }
       loc = warp_sum(loc);
       hv = warp_sum(hv);
@@ -1050,6 +1068,9 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
       // tiles of kThreads keys; the next tile's counters are loaded while the
       // current one is scanned and written (the block scan synchronises)
       const bool by_window = !kPPR && a.sched == FG_SCHED_PRIORITY;
+      const uint32_t round_max = (!kPPR && a.sched == FG_SCHED_MAXOPS)
+                                     ? *reinterpret_cast<volatile unsigned *>(&c->max_ops[round & 1u])
+                                     : 0u;
       uint32_t nx_ops = 0, nx_dirty = 0, nx_prio = kInf, nx_qb = kInf;
       {
         const uint64_t k = k0 + threadIdx.x;
@@ -1088,6 +1109,13 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
           uint32_t fl = dflag ? 1u : 0u;
           if (!kPPR) {
             if (by_window && pr > sat_add_u32(qb, window)) fl |= 2u;
+            // Max-#ops and Random (Tab. 4A) in round form: a buffer without
+            // carried-over work waits one round when it holds under a quarter
+            // of the round's largest buffer, or when a coin drawn from (key,
+            // round) says so; it then carries its work and is taken next round
+            if (dflag == 0u && a.sched == FG_SCHED_MAXOPS && 4ull * (unsigned long long)n_ops < round_max)
+              fl |= 2u;
+            if (dflag == 0u && a.sched == FG_SCHED_RANDOM && (sched_coin((uint32_t)k, round) & 1u)) fl |= 2u;
             a.prio[k] = kInf;
           }
           a.items[item_idx] = make_uint4((uint32_t)k, off, n_ops, fl);
@@ -1113,6 +1141,7 @@ __global__ void __launch_bounds__(kThreads, 3) engine_kernel(EngineArgs a) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         c->e_cursor = 0ull;
         c->item_next = 0u;
+        c->max_ops[(round + 1u) & 1u] = 0u;
       }
       if (threadIdx.x == 0) {  // visible to the block after the barrier below
         s_claim = 0ull;

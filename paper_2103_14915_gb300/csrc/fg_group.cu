@@ -8,24 +8,24 @@
 // memory system moves a whole 32- to 64-byte granule for it. Here the state of
 // a group is vertex-major, D[group][v][0..G), so the G values of one vertex
 // share one line: a relaxation of arc (v, u) is done for every query of the
-// group at once, and one line transfer serves G lanes. The partition's CSR
-// (row offsets, targets, weights) is likewise read once per (partition, group)
+// group at once, and one line access serves G lanes. The partition's CSR (row
+// offsets, targets, weights) is likewise read once per (partition, group)
 // visit for all G queries (the sharing of Sec. 3.2 and App. B.1, with the
 // buckets keyed by (partition, group): K = |Q| / G).
 //
 // Rounds (one persistent cooperative launch, two device-wide barriers each):
 //   SCAN     collect work items: every (partition, group) whose dirty flag was
 //            set in the previous round, and every pending hub vertex (more than
-//            hub_min arcs) cut into chunks of at most hub_chunk arcs
-//   PROCESS  each block claims items. A partition item stages the partition's
-//            row offsets and its pending masks into shared memory with one 1-D
-//            TMA bulk phase, lists the pending vertices and relaxes their arcs
-//            for the lanes marked pending; a hub chunk relaxes one range of a
-//            hub's arcs.
-// Arcs are relaxed 32 at a time per warp, one arc per lane: the lane copies
-// its arc's target line (the G current values) into the warp's shared memory
-// with 16-byte cp.async copies, two such steps in flight, while the lanes of
-// each query compare the previous step's values with their new ones.
+//            kHubMin arcs) cut into chunks of at most hub_chunk arcs
+//   PROCESS  in each block, one producer warp claims items, stages a partition
+//            item's row offsets and pending masks into one of two shared-memory
+//            buffers with a 1-D TMA bulk phase, lists the pending vertices and
+//            publishes the item; eight consumer warps take batches of the
+//            published item (32 listed vertices, or 32 arcs of a hub chunk)
+//            and move on to the other buffer's item when it runs out, so no
+//            warp waits for the others between items. Each buffer has a "full"
+//            barrier (the producer's arrival) and an "empty" barrier (one
+//            arrival per consumer warp) that gate its reuse.
 //
 // Operations for other partitions are consolidated where they land (Sec. 4.2
 // with one slot per (query, vertex)): a relaxation that lowers the target's
@@ -43,16 +43,28 @@
 
 namespace fg {
 
-constexpr int kGThreads = 256;
-constexpr int kGWarps = kGThreads / 32;
-constexpr int kGUnroll = 8;  // arc slots per lane group compared per inner step
+constexpr int kGCons = 8;                    // consumer warps per block
+constexpr int kGThreads = (kGCons + 1) * 32;  // and one producer warp
+constexpr int kGUnroll = 8;                  // arc slots per lane group with loads in flight at once
 
-// Shared memory of one block: the item buffers, then per warp two [32][G]
-// step buffers of target lines and one [32][G] table of source values.
+enum : uint32_t { kItemPart = 0, kItemHub = 1, kItemEnd = 2 };
+
+// A published item (one per buffer).
+struct ItemDesc {
+  uint32_t kind;  // kItemPart, kItemHub or kItemEnd (no more items this round)
+  uint32_t grp;   // group
+  uint32_t pv;    // partition (kItemPart) or hub vertex (kItemHub)
+  uint32_t n;     // listed vertices (kItemPart) or steps of 32 arcs (kItemHub)
+  uint32_t eb, ee, m;  // hub chunk: arc range and the lanes pending on the hub
+  uint32_t next;  // claim counter of the consumers (vertices or steps)
+};
+
+// Shared memory: two item buffers (row offsets, pending masks, listed
+// vertices, their arc prefix), then one [32][G] table of source values per
+// consumer warp.
 __host__ __device__ inline size_t group_item_words(int S) { return (size_t)(S + 4) * 2 + (size_t)S * 2; }
-__host__ __device__ inline size_t group_warp_words(int G) { return (size_t)3 * 32u * (size_t)G; }
 __host__ __device__ inline size_t group_smem_bytes(int S, int G) {
-  return (group_item_words(S) + (size_t)kGWarps * group_warp_words(G)) * sizeof(uint32_t);
+  return (2 * group_item_words(S) + (size_t)kGCons * 32u * (size_t)G) * sizeof(uint32_t);
 }
 
 __device__ __forceinline__ uint32_t g_relax(Ctrl *c, uint32_t d, uint32_t w) {
@@ -64,144 +76,85 @@ __device__ __forceinline__ uint32_t g_relax(Ctrl *c, uint32_t d, uint32_t w) {
   return (uint32_t)s;
 }
 
-// Block-wide exclusive scan of one u64 per thread (kGThreads threads).
-__device__ __forceinline__ unsigned long long g_block_scan(unsigned long long x, unsigned long long *s_warp,
-                                                           unsigned long long &total) {
-  const int lane = lane_id(), wid = threadIdx.x >> 5;
-  const unsigned long long incl = warp_incl_scan(x);
-  if (lane == 31) s_warp[wid] = incl;
-  block_sync();
-  if (wid == 0) {
-    const unsigned long long v = lane < kGWarps ? s_warp[lane] : 0ull;
-    const unsigned long long vi = warp_incl_scan(v);
-    if (lane < kGWarps) s_warp[lane] = vi - v;
-    if (lane == kGWarps - 1) s_warp[kGWarps] = vi;
-  }
-  block_sync();
-  const unsigned long long ex = s_warp[wid] + incl - x;
-  total = s_warp[kGWarps];
-  block_sync();
-  return ex;
-}
-
-// One step's arcs: lane l holds arc l (target u, weight w, owner o = row of the
-// warp's source-value table, has = the arc exists).
-struct ArcStep {
-  uint32_t u, w, o;
-  bool has;
-};
-
-// The lane copies its arc's target line (G values, G / 4 copies of 16 bytes)
-// into row `lane` of the step buffer, and closes the step's copy group.
-__device__ __forceinline__ void g_issue(const ArcStep &s, uint32_t *buf, const uint32_t *Dg, int G, int glog2,
-                                        int lane) {
-  if (s.has) {
-    const uint32_t *src = Dg + ((size_t)s.u << glog2);
-    uint32_t *dst = buf + ((uint32_t)lane << glog2);
-    for (int k = 0; k < G; k += 4) cp_async16_cg(dst + k, src + k);
-  }
-  cp_async_commit();
-}
-
-// Compare and lower. Lane (h, g) takes arc slot sl = j * SL + h and query g:
-// its source value (from sdv[owner][g], or dv_own for a hub chunk), the new
-// value through the arc, and the target's value copied into buf[sl][g] (a
-// snapshot: values only decrease, so an older value is an upper bound and can
-// only let a useless write through). Lanes whose new value is smaller write it
-// with atomicMin and mark the target pending for the next round.
+// One step of up to 32 arcs. Lane l holds arc l of the step (target au,
+// weight aw, owner ao = row of sdv, present ahas). The arcs are relaxed SL at
+// a time, one per lane group, kGUnroll groups in flight: each lane reads its
+// query's current value of the target (a plain load: values only decrease, so
+// a stale copy is an upper bound and can only let a useless write through),
+// and only lanes whose new value is smaller lower it with a fire-and-forget
+// atomicMin and mark the target pending for the next round. The source value
+// of lane g comes from sdv[ao * G + g] (kInf: lane not pending), or is dv_own
+// when sdv is null (a hub chunk: one source vertex).
 template <int QT>
-__device__ __forceinline__ void g_process(const GroupArgs &a, const ArcStep &s, const uint32_t *buf,
-                                          const uint32_t *sdv, uint32_t dv_own, uint32_t *Dg, uint32_t *pend_g,
-                                          uint32_t *dirty_g, uint32_t *gbest_n, int g, int h, int SL,
-                                          unsigned long long &relaxed, unsigned long long &improved) {
+__device__ __forceinline__ void g_step(const GroupArgs &a, uint32_t au, uint32_t aw, uint32_t ao, bool ahas,
+                                       const uint32_t *sdv, uint32_t dv_own, uint32_t *Dg, uint32_t *pend_g,
+                                       uint32_t *dirty_g, uint32_t *gbest_n, int g, int h, int SL,
+                                       unsigned long long &relaxed, unsigned long long &improved) {
   const int G_ = a.G;
   const unsigned gmask = G_ == 32 ? 0xFFFFFFFFu : ((1u << G_) - 1u);
   const int slog2 = a.g.slog2;
   for (int j0 = 0; j0 < 32; j0 += SL * kGUnroll) {
+    uint32_t u[kGUnroll], nd[kGUnroll], cur[kGUnroll];
+    bool act[kGUnroll];
 #pragma unroll
     for (int q = 0; q < kGUnroll; ++q) {
       const int sl = j0 + q * SL + h;  // < 32: 32 is a multiple of SL * kGUnroll
-      const uint32_t uu = __shfl_sync(kFull, s.u, sl);
-      const uint32_t ww = __shfl_sync(kFull, s.w, sl);
-      const uint32_t oo = __shfl_sync(kFull, s.o, sl);
-      const bool hh = __shfl_sync(kFull, s.has ? 1u : 0u, sl) != 0u;
+      const uint32_t uu = __shfl_sync(kFull, au, sl);
+      const uint32_t ww = __shfl_sync(kFull, aw, sl);
+      const uint32_t oo = __shfl_sync(kFull, ao, sl);
+      const bool hh = __shfl_sync(kFull, ahas ? 1u : 0u, sl) != 0u;
       uint32_t dv = kInf;
       if (hh) dv = sdv != nullptr ? sdv[(oo << a.glog2) + (uint32_t)g] : dv_own;
-      const bool act = hh && dv != kInf;
-      const uint32_t nd = act ? g_relax(a.ctrl, dv, QT == Q_BFS ? 1u : ww) : kInf;
-      const uint32_t cur = act ? buf[((uint32_t)sl << a.glog2) + (uint32_t)g] : 0u;
-      const bool imp = act && nd < cur;
-      relaxed += act ? 1ull : 0ull;
-      if (imp) atomicMin(Dg + ((size_t)uu << a.glog2) + (size_t)g, nd);
+      act[q] = hh && dv != kInf;
+      nd[q] = act[q] ? g_relax(a.ctrl, dv, QT == Q_BFS ? 1u : ww) : kInf;
+      u[q] = uu;
+      cur[q] = act[q] ? Dg[((size_t)uu << a.glog2) + (size_t)g] : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < kGUnroll; ++q) {
+      const bool imp = act[q] && nd[q] < cur[q];
+      relaxed += act[q] ? 1ull : 0ull;
+      if (imp) atomicMin(Dg + ((size_t)u[q] << a.glog2) + (size_t)g, nd[q]);
       const unsigned im = __ballot_sync(kFull, imp);
       const unsigned mine = (im >> (h * G_)) & gmask;
       if (mine != 0u && g == 0) {
-        atomicOr(pend_g + uu, mine);
-        dirty_g[uu >> slog2] = 1u;
+        atomicOr(pend_g + u[q], mine);
+        dirty_g[u[q] >> slog2] = 1u;
         improved += (unsigned long long)__popc(mine);
       }
       if (gbest_n != nullptr) {
         // smallest new value of the group, for the next round's window
-        const uint32_t mn = __reduce_min_sync(kFull, imp ? nd : kInf);
+        const uint32_t mn = __reduce_min_sync(kFull, imp ? nd[q] : kInf);
         if (mn != kInf && (threadIdx.x & 31) == 0) atomicMin(gbest_n, mn);
       }
     }
   }
 }
 
-// Relax a sequence of nsteps steps of 32 arcs, the copies of step i + 1 in
-// flight while step i is compared. make(i) fills a step (warp-collective).
-template <int QT, typename Make>
-__device__ __forceinline__ void g_run_steps(const GroupArgs &a, uint32_t nsteps, Make make, uint32_t *wbuf,
-                                            const uint32_t *sdv, uint32_t dv_own, uint32_t *Dg, uint32_t *pend_g,
-                                            uint32_t *dirty_g, uint32_t *gbest_n, int g, int h, int SL, int lane,
-                                            unsigned long long &relaxed, unsigned long long &improved,
-                                            unsigned long long &arcs) {
-  if (nsteps == 0u) return;
-  const int G_ = a.G;
-  uint32_t *buf[2] = {wbuf, wbuf + 32 * G_};
-  ArcStep cur = make(0u);
-  g_issue(cur, buf[0], Dg, G_, a.glog2, lane);
-  for (uint32_t i = 0; i < nsteps; ++i) {
-    ArcStep nxt{0u, 0u, 0u, false};
-    if (i + 1u < nsteps) {
-      nxt = make(i + 1u);
-      g_issue(nxt, buf[(i + 1u) & 1u], Dg, G_, a.glog2, lane);
-    } else {
-      cp_async_commit();  // an empty group keeps "all but the newest group" meaning step i
-    }
-    cp_async_wait<1>();
-    __syncwarp();
-    arcs += cur.has ? 1ull : 0ull;
-    g_process<QT>(a, cur, buf[i & 1u], sdv, dv_own, Dg, pend_g, dirty_g, gbest_n, g, h, SL, relaxed, improved);
-    __syncwarp();  // buf[i & 1] is refilled by step i + 2
-    cur = nxt;
-  }
-  cp_async_wait<0>();
-}
-
 template <int QT>
-__global__ void __launch_bounds__(kGThreads, 2) group_kernel(GroupArgs a) {
+__global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
   extern __shared__ __align__(16) uint32_t g_smem[];
-  __shared__ __align__(8) uint64_t s_bar;
-  __shared__ unsigned long long s_scan[kGWarps + 1];
-  __shared__ uint32_t s_item, s_batch, s_cnt;
+  __shared__ __align__(8) uint64_t s_full[2], s_empty[2], s_tma[2];
+  __shared__ ItemDesc s_desc[2];
   const int lane = lane_id(), wid = threadIdx.x >> 5;
+  const bool producer = wid == kGCons;
   const DevGraph &G = a.g;
   const int S = G.S;
   const int Gq = a.G;
   const int g = lane & (Gq - 1);     // query of the group held by this lane
   const int h = lane >> a.glog2;     // arc slot of this lane
   const int SL = 32 >> a.glog2;      // arc slots per warp
-  uint32_t *s_rp = g_smem;           // [S + 4] row offsets of the item's partition
-  uint32_t *s_pm = s_rp + (S + 4);   // [S]     pending masks of the item's group
-  uint32_t *s_vid = s_pm + S;        // [S]     pending vertices (partition-local), listed
-  uint32_t *s_pre = s_vid + S;       // [S + 4] exclusive prefix of their arc counts
-  uint32_t *wbuf = s_pre + (S + 4) + (size_t)wid * group_warp_words(Gq);  // 2 x [32][G] step buffers
-  uint32_t *sdv = wbuf + 64 * Gq;                                          // [32][G] source values
+  const size_t iw = group_item_words(S);
+  // item buffer k: rp [S + 4], pm [S], vid [S], pre [S + 4]
+  auto buf_rp = [&](uint32_t k) { return g_smem + k * iw; };
+  auto buf_pm = [&](uint32_t k) { return g_smem + k * iw + (S + 4); };
+  auto buf_vid = [&](uint32_t k) { return g_smem + k * iw + (S + 4) + S; };
+  auto buf_pre = [&](uint32_t k) { return g_smem + k * iw + (S + 4) + 2 * S; };
+  uint32_t *sdv = g_smem + 2 * iw + (size_t)(producer ? 0 : wid) * 32u * (uint32_t)Gq;  // [32][G]
   Ctrl *c = a.ctrl;
   unsigned gen = *reinterpret_cast<volatile unsigned *>(&c->bar_gen);
-  uint32_t phase = 0;
+  uint32_t it_base = 0;   // items this block has gone through (both buffers), the same in every warp
+  uint32_t tma_bits = 0;  // producer: phase parity of s_tma[0] (bit 0) and s_tma[1] (bit 1)
   unsigned long long n_relaxed = 0, n_improved = 0, n_visits = 0, n_arcs = 0;
   uint64_t t_prev = (blockIdx.x == 0 && threadIdx.x == 0) ? global_ns() : 0ull;
   unsigned long long ph[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
@@ -215,7 +168,11 @@ __global__ void __launch_bounds__(kGThreads, 2) group_kernel(GroupArgs a) {
   } while (0)
 
   if (threadIdx.x == 0) {
-    mbar_init(&s_bar, 1);
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&s_full[k], 1);
+      mbar_init(&s_empty[k], kGCons);
+      mbar_init(&s_tma[k], 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     fence_proxy_async_smem();
   }
@@ -315,183 +272,195 @@ __global__ void __launch_bounds__(kGThreads, 2) group_kernel(GroupArgs a) {
       c->rounds += 1ull;
       if ((unsigned long long)n_hub + n_reg > c->max_round_ops) c->max_round_ops = (unsigned long long)n_hub + n_reg;
     }
-    const uint32_t bound_w = a.window;
     // ---- PROCESS ----
-    for (;;) {
-      if (threadIdx.x == 0) {
-        uint32_t idx = atomicAdd(&c->g_next[cur], 1u);
-        if (ld_volatile_i32(&c->abort)) idx = n_hub + n_reg;
-        s_item = idx;
-        s_batch = 0u;
-      }
-      block_sync();
-      const uint32_t idx = s_item;
-      if (idx >= n_hub + n_reg) break;
-      if (idx < n_hub) {
-        // -- one chunk of a hub's arcs, for the lanes pending on it --
-        const uint4 it = __ldcg(a.items + idx);
-        const uint32_t grp = it.x, v = it.y, eb = it.z, m = it.w;
-        const uint32_t e1 = G.rp[v + 1];
-        const uint32_t ee = eb + a.hub_chunk < e1 ? eb + a.hub_chunk : e1;
-        uint32_t *Dg = a.D + (size_t)grp * row * (size_t)Gq;
-        uint32_t dv = kInf;
-        if (((m >> g) & 1u) != 0u) dv = __ldcg(Dg + ((size_t)v << a.glog2) + (size_t)g);
-        uint32_t *gb_n = a.gbest ? a.gbest + (size_t)nxt * a.ngroups + grp : nullptr;
-        // the warp takes steps wid, wid + 8, ... of 32 consecutive arcs
-        const uint32_t total = ee - eb;
-        const uint32_t all_steps = (total + 31u) / 32u;
-        const uint32_t my_steps = all_steps > (uint32_t)wid ? (all_steps - 1u - (uint32_t)wid) / kGWarps + 1u : 0u;
-        auto make = [&](uint32_t i) {
-          ArcStep st;
-          const uint32_t e = eb + ((uint32_t)wid + i * kGWarps) * 32u + (uint32_t)lane;
-          st.has = e < ee;
-          st.u = st.has ? __ldg(G.adj + e) : 0u;
-          st.w = (st.has && QT != Q_BFS && G.wt != nullptr) ? __ldg(G.wt + e) : 1u;
-          st.o = 0u;
-          return st;
-        };
-        g_run_steps<QT>(a, my_steps, make, wbuf, nullptr, dv, Dg, pend_n + (size_t)grp * row,
-                        dirty_n + (size_t)grp * G.nparts, gb_n, g, h, SL, lane, n_relaxed, n_improved, n_arcs);
-        if (threadIdx.x == 0) ++n_visits;
-        block_sync();
-        continue;
-      }
-      // -- a (partition, group) item --
-      const uint4 it = __ldcg(a.items + a.hub_cap + (idx - n_hub));
-      const uint32_t key = it.x;
-      const uint32_t grp = key / (uint32_t)G.nparts, p = key - grp * (uint32_t)G.nparts;
-      const uint32_t base = p << G.slog2;
-      uint32_t *pm_g = pend_c + (size_t)grp * row + base;
-      // 1. stage the partition's row offsets and the group's pending masks
-      //    (one bulk phase; the expected bytes are announced before the copies)
-      if (threadIdx.x == 0) {
-        const uint32_t b_rp = (uint32_t)(S + 4) * 4u, b_pm = (uint32_t)S * 4u;
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&s_bar, b_rp + b_pm);
-        bulk_g2s(s_rp, G.rp + base, b_rp, &s_bar);
-        bulk_g2s(s_pm, pm_g, b_pm, &s_bar);
-      }
-      {
-        // the outcome is made block-uniform, so no thread leaves the item alone
-        const int ok = __syncthreads_and(mbar_wait(&s_bar, phase, a.watchdog_ns) ? 1 : 0);
-        if (!ok) {
-          if (threadIdx.x == 0) {
-            raise_status(c, FG_ERR_TIMEOUT, kSiteStage);
-            (void)mbar_wait(&s_bar, phase, 1000000ull);  // the copies in flight, once more, bounded
+    if (producer) {
+      // -- claim, stage, list, publish; every wait is bounded --
+      uint32_t it = it_base;
+      for (;;) {
+        const uint32_t k = it & 1u, use = it >> 1;
+        // every wait's outcome is made warp-uniform before anyone acts on it
+        if (use > 0u && !__all_sync(kFull, mbar_wait(&s_empty[k], (use - 1u) & 1u, a.watchdog_ns))) {
+          if (lane == 0) raise_status(c, FG_ERR_TIMEOUT, kSiteStage);
+          break;  // the consumers time out on their own waits
+        }
+        uint32_t idx = 0;
+        if (lane == 0) {
+          idx = atomicAdd(&c->g_next[cur], 1u);
+          if (ld_volatile_i32(&c->abort)) idx = n_hub + n_reg;
+        }
+        idx = __shfl_sync(kFull, idx, 0);
+        ItemDesc d{kItemEnd, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        if (idx < n_hub) {
+          const uint4 itm = __ldcg(a.items + idx);
+          const uint32_t e1 = G.rp[itm.y + 1];
+          d.kind = kItemHub;
+          d.grp = itm.x;
+          d.pv = itm.y;
+          d.eb = itm.z;
+          d.ee = itm.z + a.hub_chunk < e1 ? itm.z + a.hub_chunk : e1;
+          d.m = itm.w;
+          d.n = (d.ee - d.eb + 31u) / 32u;
+        } else if (idx < n_hub + n_reg) {
+          const uint32_t key = __ldcg(a.items + a.hub_cap + (idx - n_hub)).x;
+          const uint32_t grp = key / (uint32_t)G.nparts, p = key - grp * (uint32_t)G.nparts;
+          const uint32_t base = p << G.slog2;
+          uint32_t *pm_g = pend_c + (size_t)grp * row + base;
+          uint32_t *rp_s = buf_rp(k), *pm_s = buf_pm(k), *vid_s = buf_vid(k), *pre_s = buf_pre(k);
+          // stage the row offsets and the group's pending masks (one bulk
+          // phase; the expected bytes are announced before the copies); the
+          // buffer's previous readers are done (empty barrier), so the proxy
+          // fence orders their reads before the bulk writes
+          if (lane == 0) {
+            const uint32_t b_rp = (uint32_t)(S + 4) * 4u, b_pm = (uint32_t)S * 4u;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&s_tma[k], b_rp + b_pm);
+            bulk_g2s(rp_s, G.rp + base, b_rp, &s_tma[k]);
+            bulk_g2s(pm_s, pm_g, b_pm, &s_tma[k]);
           }
-          block_sync();
+          const uint32_t par = (tma_bits >> k) & 1u;
+          const bool ok = __all_sync(kFull, mbar_wait(&s_tma[k], par, a.watchdog_ns));
+          if (!ok) {
+            if (lane == 0) {
+              raise_status(c, FG_ERR_TIMEOUT, kSiteStage);
+              (void)mbar_wait(&s_tma[k], par, 1000000ull);  // the copies in flight, once more, bounded
+            }
+            break;
+          }
+          tma_bits ^= 1u << k;
+          // this round's masks of the item are taken: clear them for reuse
+          for (int i = lane; i < (S >> 2); i += 32) reinterpret_cast<uint4 *>(pm_g)[i] = make_uint4(0u, 0u, 0u, 0u);
+          // list the pending vertices with an arc, and the prefix of their arcs
+          uint32_t cnt = 0, arcs = 0;
+          for (int i0 = 0; i0 < S; i0 += 32) {
+            const int i = i0 + lane;
+            const uint32_t deg = rp_s[i + 1] - rp_s[i];
+            const bool keep = pm_s[i] != 0u && deg > 0u;
+            const unsigned bm = __ballot_sync(kFull, keep);
+            const uint32_t dk = keep ? deg : 0u;
+            const uint32_t incl = warp_incl_scan(dk);
+            if (keep) {
+              const uint32_t pos = cnt + (uint32_t)__popc(bm & ((1u << lane) - 1u));
+              vid_s[pos] = (uint32_t)i;
+              pre_s[pos] = arcs + incl - dk;
+            }
+            cnt += (uint32_t)__popc(bm);
+            arcs += __shfl_sync(kFull, incl, 31);
+          }
+          d.kind = kItemPart;
+          d.grp = grp;
+          d.pv = p;
+          d.n = cnt;
+        }
+        if (lane == 0) {
+          s_desc[k] = d;
+          if (d.kind != kItemEnd) ++n_visits;
+        }
+        __syncwarp();  // every lane's list writes precede the publishing arrival
+        if (lane == 0) mbar_arrive(&s_full[k]);
+        ++it;
+        if (d.kind == kItemEnd) break;
+      }
+      it_base = it;
+    } else {
+      // -- consumers: batches of the published items, in order --
+      uint32_t it = it_base;
+      for (;;) {
+        const uint32_t k = it & 1u, use = it >> 1;
+        if (!__all_sync(kFull, mbar_wait(&s_full[k], use & 1u, a.watchdog_ns))) {
+          if (lane == 0) raise_status(c, FG_ERR_TIMEOUT, kSiteStage);
           break;
         }
-      }
-      phase ^= 1u;
-      // 2. this round's masks of the item are taken: clear them for reuse
-      for (int i = threadIdx.x; i < (S >> 2); i += kGThreads)
-        reinterpret_cast<uint4 *>(pm_g)[i] = make_uint4(0u, 0u, 0u, 0u);
-      uint32_t *Dg = a.D + (size_t)grp * row * (size_t)Gq;
-      uint32_t *gb_n = a.gbest ? a.gbest + (size_t)nxt * a.ngroups + grp : nullptr;
-      // 3. window (Delta-stepping across rounds): lanes whose value is at or
-      //    beyond the group's bound stay pending for a later round
-      if (bound_w != 0u && a.gbest != nullptr) {
-        const uint32_t bound = sat_add_u32(__ldcg(a.gbest + (size_t)cur * a.ngroups + grp), bound_w);
-        for (int i0 = wid * SL; i0 < S; i0 += kGWarps * SL) {
-          const int i = i0 + h;
-          const uint32_t m = s_pm[i];
-          bool def = false;
+        const ItemDesc d = s_desc[k];
+        ++it;
+        if (d.kind == kItemEnd) {
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&s_empty[k]);
+          break;
+        }
+        uint32_t *Dg = a.D + (size_t)d.grp * row * (size_t)Gq;
+        uint32_t *pend_g = pend_n + (size_t)d.grp * row;
+        uint32_t *dirty_g = dirty_n + (size_t)d.grp * G.nparts;
+        uint32_t *gb_n = a.gbest ? a.gbest + (size_t)nxt * a.ngroups + d.grp : nullptr;
+        if (d.kind == kItemHub) {
           uint32_t dv = kInf;
-          if (((m >> g) & 1u) != 0u) {
-            dv = __ldcg(Dg + ((size_t)(base + (uint32_t)i) << a.glog2) + (size_t)g);
-            def = dv >= bound;
+          if (((d.m >> g) & 1u) != 0u) dv = __ldcg(Dg + ((size_t)d.pv << a.glog2) + (size_t)g);
+          for (;;) {
+            uint32_t s = 0;
+            if (lane == 0) s = atomicAdd(&s_desc[k].next, 1u);
+            s = __shfl_sync(kFull, s, 0);
+            if (s >= d.n) break;
+            const uint32_t e = d.eb + s * 32u + (uint32_t)lane;
+            const bool has = e < d.ee;
+            const uint32_t au = has ? __ldg(G.adj + e) : 0u;
+            const uint32_t aw = (has && QT != Q_BFS && G.wt != nullptr) ? __ldg(G.wt + e) : 1u;
+            n_arcs += has ? 1ull : 0ull;
+            g_step<QT>(a, au, aw, 0u, has, nullptr, dv, Dg, pend_g, dirty_g, gb_n, g, h, SL, n_relaxed, n_improved);
           }
-          const unsigned dm = __ballot_sync(kFull, def);
-          const unsigned gmask = Gq == 32 ? 0xFFFFFFFFu : ((1u << Gq) - 1u);
-          const unsigned mine = (dm >> (h * Gq)) & gmask;
-          const uint32_t mn = __reduce_min_sync(kFull, def ? dv : kInf);
-          if (mine != 0u && g == 0) {
-            atomicOr(pend_n + (size_t)grp * row + base + (uint32_t)i, mine);
-            dirty_n[(size_t)grp * G.nparts + p] = 1u;
-            s_pm[i] = m & ~mine;
-          }
-          if (mn != kInf && lane == 0) atomicMin(gb_n, mn);
-        }
-        block_sync();
-      }
-      // 4. list the pending vertices and the exclusive prefix of their arcs
-      {
-        const int per = (S + kGThreads - 1) / kGThreads;
-        unsigned long long x = 0;
-        for (int j = 0; j < per; ++j) {
-          const int i = threadIdx.x * per + j;
-          if (i < S && s_pm[i] != 0u) {
-            const uint32_t deg = s_rp[i + 1] - s_rp[i];
-            if (deg > 0u) x += (1ull << 32) | (unsigned long long)deg;
-          }
-        }
-        unsigned long long tot;
-        unsigned long long ex = g_block_scan(x, s_scan, tot);
-        for (int j = 0; j < per; ++j) {
-          const int i = threadIdx.x * per + j;
-          if (i < S && s_pm[i] != 0u) {
-            const uint32_t deg = s_rp[i + 1] - s_rp[i];
-            if (deg > 0u) {
-              const uint32_t pos = (uint32_t)(ex >> 32);
-              s_vid[pos] = (uint32_t)i;
-              s_pre[pos] = (uint32_t)ex;
-              ex += (1ull << 32) | (unsigned long long)deg;
+        } else {
+          const uint32_t base = d.pv << G.slog2;
+          const uint32_t *rp_s = buf_rp(k), *pm_s = buf_pm(k), *vid_s = buf_vid(k);
+          const uint32_t bound =
+              (a.window != 0u && a.gbest != nullptr)
+                  ? sat_add_u32(__ldcg(a.gbest + (size_t)cur * a.ngroups + d.grp), a.window)
+                  : kInf;
+          for (;;) {
+            uint32_t b0 = 0;
+            if (lane == 0) b0 = atomicAdd(&s_desc[k].next, 32u);
+            b0 = __shfl_sync(kFull, b0, 0);
+            if (b0 >= d.n) break;
+            const uint32_t j = b0 + (uint32_t)lane;
+            const bool valid = j < d.n;
+            const uint32_t li = valid ? vid_s[j] : 0u;
+            const uint32_t m = valid ? pm_s[li] : 0u;
+            const uint32_t a0 = valid ? rp_s[li] : 0u;
+            const uint32_t deg = valid ? rp_s[li + 1] - a0 : 0u;
+            const uint32_t incl = warp_incl_scan(deg);
+            const uint32_t exd = incl - deg;
+            const uint32_t tot = __shfl_sync(kFull, incl, 31);
+            // the batch's source values, fresh from L2 (the pending bit was set
+            // because the value fell; an older copy could miss that fall): row
+            // L of sdv holds vertex L's values of the group, kInf where not
+            // pending. Under a window, values at or beyond the group's bound
+            // stay pending for a later round (Delta-stepping across rounds).
+            for (int L0 = 0; L0 < 32; L0 += SL) {
+              const int L = L0 + h;
+              const uint32_t vL = __shfl_sync(kFull, li, L);
+              const uint32_t mL = __shfl_sync(kFull, m, L);
+              uint32_t dd = kInf;
+              if (((mL >> g) & 1u) != 0u) dd = __ldcg(Dg + ((size_t)(base + vL) << a.glog2) + (size_t)g);
+              const bool def = dd != kInf && dd >= bound;
+              const unsigned dm = __ballot_sync(kFull, def);
+              const unsigned gmask = Gq == 32 ? 0xFFFFFFFFu : ((1u << Gq) - 1u);
+              const unsigned mine = (dm >> (h * Gq)) & gmask;
+              if (mine != 0u && g == 0) {
+                atomicOr(pend_g + base + vL, mine);
+                dirty_g[d.pv] = 1u;
+              }
+              if (gb_n != nullptr) {
+                const uint32_t mn = __reduce_min_sync(kFull, def ? dd : kInf);
+                if (mn != kInf && lane == 0) atomicMin(gb_n, mn);
+              }
+              sdv[(L << a.glog2) + g] = def ? kInf : dd;
             }
+            __syncwarp();
+            for (uint32_t t0 = 0; t0 < tot; t0 += 32u) {
+              const uint32_t t = t0 + (uint32_t)lane;
+              const bool has = t < tot;
+              const int L = owner_lane(exd, has ? t : 0u);
+              const uint32_t eL = __shfl_sync(kFull, a0, L) + (t - __shfl_sync(kFull, exd, L));
+              const uint32_t au = has ? __ldg(G.adj + eL) : 0u;
+              const uint32_t aw = (has && QT != Q_BFS && G.wt != nullptr) ? __ldg(G.wt + eL) : 1u;
+              n_arcs += has ? 1ull : 0ull;
+              g_step<QT>(a, au, aw, (uint32_t)L, has, sdv, kInf, Dg, pend_g, dirty_g, gb_n, g, h, SL, n_relaxed,
+                         n_improved);
+            }
+            __syncwarp();  // sdv is rewritten by the next batch
           }
-        }
-        if (threadIdx.x == 0) {
-          s_cnt = (uint32_t)(tot >> 32);
-          s_pre[tot >> 32] = (uint32_t)tot;
-        }
-        block_sync();
-      }
-      const uint32_t nv = s_cnt;
-      // 5. relax: warps take batches of up to 32 listed vertices; the batch's
-      //    arcs are cut into steps of 32 (merge path over the batch's lanes)
-      for (;;) {
-        uint32_t b0 = 0;
-        if (lane == 0) b0 = atomicAdd(&s_batch, 32u);
-        b0 = __shfl_sync(kFull, b0, 0);
-        if (b0 >= nv) break;
-        const uint32_t j = b0 + (uint32_t)lane;
-        const bool valid = j < nv;
-        const uint32_t li = valid ? s_vid[j] : 0u;
-        const uint32_t m = valid ? s_pm[li] : 0u;
-        const uint32_t a0 = valid ? s_rp[li] : 0u;
-        const uint32_t deg = valid ? s_rp[li + 1] - a0 : 0u;
-        const uint32_t incl = warp_incl_scan(deg);
-        const uint32_t exd = incl - deg;
-        const uint32_t tot = __shfl_sync(kFull, incl, 31);
-        // the batch's source values, fresh from L2 (the pending bit was set
-        // because the value fell; an older copy could miss that fall): row L
-        // of sdv holds vertex L's values of the group, kInf where not pending
-        for (int L0 = 0; L0 < 32; L0 += SL) {
-          const int L = L0 + h;
-          const uint32_t vL = __shfl_sync(kFull, li, L);
-          const uint32_t mL = __shfl_sync(kFull, m, L);
-          uint32_t d = kInf;
-          if (((mL >> g) & 1u) != 0u) d = __ldcg(Dg + ((size_t)(base + vL) << a.glog2) + (size_t)g);
-          sdv[(L << a.glog2) + g] = d;
         }
         __syncwarp();
-        auto make = [&](uint32_t i) {
-          ArcStep st;
-          const uint32_t t = i * 32u + (uint32_t)lane;
-          st.has = t < tot;
-          const int L = owner_lane(exd, st.has ? t : 0u);
-          const uint32_t eL = __shfl_sync(kFull, a0, L) + (t - __shfl_sync(kFull, exd, L));
-          st.u = st.has ? __ldg(G.adj + eL) : 0u;
-          st.w = (st.has && QT != Q_BFS && G.wt != nullptr) ? __ldg(G.wt + eL) : 1u;
-          st.o = (uint32_t)L;
-          return st;
-        };
-        g_run_steps<QT>(a, (tot + 31u) / 32u, make, wbuf, sdv, kInf, Dg, pend_n + (size_t)grp * row,
-                        dirty_n + (size_t)grp * G.nparts, gb_n, g, h, SL, lane, n_relaxed, n_improved, n_arcs);
-        __syncwarp();  // sdv is rewritten by the next batch
+        if (lane == 0) mbar_arrive(&s_empty[k]);  // this warp is done with buffer k
       }
-      if (threadIdx.x == 0) ++n_visits;
-      block_sync();  // shared buffers and s_item are reused by the next item
+      it_base = it;
     }
     if (!grid_barrier(c, gen, a.watchdog_ns)) goto done;
     FG_GPHASE(5);
@@ -504,12 +473,13 @@ done:
   }
   {
     const unsigned long long r = warp_sum(n_relaxed), im = warp_sum(n_improved), ar = warp_sum(n_arcs);
+    const unsigned long long vi = warp_sum(n_visits);
     if (lane == 0) {
       atomicAdd(&c->edges, r);
       atomicAdd(&c->ops, im);
       atomicAdd(&c->arcs_read, ar);
+      atomicAdd(&c->visits, vi);
     }
-    if (threadIdx.x == 0) atomicAdd(&c->visits, n_visits);
   }
 }
 

@@ -49,6 +49,7 @@ struct Ctrl {
   // partition items) and the claiming counter
   unsigned int g_hub_items[2], g_items[2], g_next[2];
   unsigned long long arcs_read;  // graph arcs read (per query visit, or per group visit)
+  unsigned int max_ops[2];       // largest buffer of the round, per round parity (max-operations scheduling)
 };
 
 struct EngineArgs {

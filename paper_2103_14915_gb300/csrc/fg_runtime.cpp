@@ -463,7 +463,7 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
   fg_opts o;
   merge_opts(opts_in, &o);
   if (o.mode != FG_MODE_BUFFERED && o.mode != FG_MODE_PLAIN) return fail(FG_ERR_INVALID_ARG, "unknown mode");
-  if (o.sched != FG_SCHED_FIFO && o.sched != FG_SCHED_PRIORITY) return fail(FG_ERR_INVALID_ARG, "unknown sched");
+  if (o.sched < FG_SCHED_FIFO || o.sched > FG_SCHED_RANDOM) return fail(FG_ERR_INVALID_ARG, "unknown sched");
   if (o.query_batch < 0) return fail(FG_ERR_INVALID_ARG, "query_batch must be >= 0");
   if (o.host_io < 0 || o.host_io > 2) return fail(FG_ERR_INVALID_ARG, "host_io must be 0, 1 or 2");
   if (o.threads_per_vertex != 0 && o.threads_per_vertex != 1 && o.threads_per_vertex != 32)

@@ -31,7 +31,7 @@ STATUS_NAMES = {0: "FG_OK", 1: "FG_ERR_INVALID_ARG", 2: "FG_ERR_OOM", 3: "FG_ERR
 
 FG_DEVICE_PTRS = 0x1
 FG_PART_AUTO, FG_PART_RANGE, FG_PART_GROW, FG_PART_DEGREE = 0, 1, 2, 3
-FG_SCHED_FIFO, FG_SCHED_PRIORITY = 0, 1
+FG_SCHED_FIFO, FG_SCHED_PRIORITY, FG_SCHED_MAXOPS, FG_SCHED_RANDOM = 0, 1, 2, 3
 FG_MODE_BUFFERED, FG_MODE_PLAIN = 0, 1
 
 

@@ -17,7 +17,7 @@ ROOT = Path(__file__).resolve().parents[1]
 def test_reference_arm_line():
     # a scale-12 R-MAT of the bench recipe keeps the CPU suite short (the box runs scale 24)
     out = subprocess.run([sys.executable, str(ROOT / "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "3", "--graph-scale", "12", "--cpu-sources", "4"], cwd=ROOT,
+                          "--warmup", "3", "--graph-scale", "12"], cwd=ROOT,
                          capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [line for line in out.stdout.splitlines() if line.startswith("{")]
@@ -28,7 +28,7 @@ def test_reference_arm_line():
         assert k in d, k
     assert d["impl"] == "reference" and d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1
     assert d["value"] > 0 and d["higher_is_better"] is True and d["vs_baseline"] is None
-    assert d["config"]["workload"] == "rmat12_sssp" and d["config"]["queries_per_step"] == 4
+    assert d["config"]["workload"] == "rmat12_sssp" and d["config"]["queries_per_step"] == 1
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0

@@ -122,6 +122,13 @@ OPTS = [
     dict(mode=fg.FG_MODE_PLAIN),
     dict(threads_per_vertex=1),
     dict(threads_per_vertex=1, delta=300, sched=fg.FG_SCHED_PRIORITY),
+    dict(sched=fg.FG_SCHED_MAXOPS),
+    dict(sched=fg.FG_SCHED_RANDOM),
+    dict(sched=fg.FG_SCHED_MAXOPS, group=1, yield_edges=4),
+    dict(sched=fg.FG_SCHED_RANDOM, group=1, delta=300),
+    dict(group=1),
+    dict(group=8),
+    dict(group=32, sched=fg.FG_SCHED_PRIORITY, sched_window=500),
 ]
 
 
