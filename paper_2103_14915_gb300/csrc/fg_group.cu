@@ -60,11 +60,11 @@ struct ItemDesc {
 };
 
 // Shared memory: two item buffers (row offsets, pending masks, listed
-// vertices, their arc prefix), then one [32][G] table of source values per
-// consumer warp.
+// vertices, their arc prefix), then per consumer warp the current step's 32
+// arcs (uint4 each) and one [32][G] table of source values.
 __host__ __device__ inline size_t group_item_words(int S) { return (size_t)(S + 4) * 2 + (size_t)S * 2; }
 __host__ __device__ inline size_t group_smem_bytes(int S, int G) {
-  return (2 * group_item_words(S) + (size_t)kGCons * 32u * (size_t)G) * sizeof(uint32_t);
+  return (2 * group_item_words(S) + (size_t)kGCons * (128u + 32u * (size_t)G)) * sizeof(uint32_t);
 }
 
 __device__ __forceinline__ uint32_t g_relax(Ctrl *c, uint32_t d, uint32_t w) {
@@ -76,62 +76,70 @@ __device__ __forceinline__ uint32_t g_relax(Ctrl *c, uint32_t d, uint32_t w) {
   return (uint32_t)s;
 }
 
-// One step of up to 32 arcs. Lane l holds arc l of the step (target au,
-// weight aw, owner ao = row of sdv, present ahas). The arcs are relaxed SL at
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x / 2); }
+
+// One step of up to 32 arcs, staged by the warp in sarc[0..32): target, weight,
+// owner row (kNoArc: no arc in this slot). The arcs are relaxed SL = 32 / GQ at
 // a time, one per lane group, kGUnroll groups in flight: each lane reads its
 // query's current value of the target (a plain load: values only decrease, so
 // a stale copy is an upper bound and can only let a useless write through),
 // and only lanes whose new value is smaller lower it with a fire-and-forget
-// atomicMin and mark the target pending for the next round. The source value
-// of lane g comes from sdv[ao * G + g] (kInf: lane not pending), or is dv_own
-// when sdv is null (a hub chunk: one source vertex).
-template <int QT>
-__device__ __forceinline__ void g_step(const GroupArgs &a, uint32_t au, uint32_t aw, uint32_t ao, bool ahas,
-                                       const uint32_t *sdv, uint32_t dv_own, uint32_t *Dg, uint32_t *pend_g,
-                                       uint32_t *dirty_g, uint32_t *gbest_n, int g, int h, int SL,
-                                       unsigned long long &relaxed, unsigned long long &improved) {
-  const int G_ = a.G;
-  const unsigned gmask = G_ == 32 ? 0xFFFFFFFFu : ((1u << G_) - 1u);
+// atomicMin; one lane per lane group then marks the target pending for the
+// next round. The source value of lane g is sdv_g[owner * GQ] (sdv_g = the
+// warp's [32][GQ] table + g; kInf: lane not pending), or dv_own when sdv_g is
+// null (a hub chunk: one source vertex). Dg_g = the group's state + g.
+constexpr uint32_t kNoArc = 0xFFFFFFFFu;
+
+template <int QT, int GQ>
+__device__ __forceinline__ void g_step(const GroupArgs &a, const uint4 *sarc, const uint32_t *sdv_g,
+                                       uint32_t dv_own, uint32_t *Dg_g, uint32_t *pend_g, uint32_t *dirty_g,
+                                       uint32_t *gbest_n, int g, int h, uint32_t &relaxed, uint32_t &improved) {
+  constexpr int LG = ilog2c(GQ), SL = 32 / GQ;
+  constexpr unsigned GM = GQ == 32 ? 0xFFFFFFFFu : ((1u << GQ) - 1u);
   const int slog2 = a.g.slog2;
+#pragma unroll
   for (int j0 = 0; j0 < 32; j0 += SL * kGUnroll) {
     uint32_t u[kGUnroll], nd[kGUnroll], cur[kGUnroll];
     bool act[kGUnroll];
 #pragma unroll
     for (int q = 0; q < kGUnroll; ++q) {
-      const int sl = j0 + q * SL + h;  // < 32: 32 is a multiple of SL * kGUnroll
-      const uint32_t uu = __shfl_sync(kFull, au, sl);
-      const uint32_t ww = __shfl_sync(kFull, aw, sl);
-      const uint32_t oo = __shfl_sync(kFull, ao, sl);
-      const bool hh = __shfl_sync(kFull, ahas ? 1u : 0u, sl) != 0u;
+      const uint4 e = sarc[j0 + q * SL + h];  // one broadcast read per lane group
       uint32_t dv = kInf;
-      if (hh) dv = sdv != nullptr ? sdv[(oo << a.glog2) + (uint32_t)g] : dv_own;
-      act[q] = hh && dv != kInf;
-      nd[q] = act[q] ? g_relax(a.ctrl, dv, QT == Q_BFS ? 1u : ww) : kInf;
-      u[q] = uu;
-      cur[q] = act[q] ? Dg[((size_t)uu << a.glog2) + (size_t)g] : 0u;
+      if (e.z != kNoArc) dv = sdv_g != nullptr ? sdv_g[e.z << LG] : dv_own;
+      act[q] = dv != kInf;
+      uint32_t sum = dv + (QT == Q_BFS ? 1u : e.y);
+      if (act[q] && (sum < dv || sum == kInf)) {  // 2^32 - 1 reached: saturate and report
+        atomicCAS(&a.ctrl->status, 0, (int)FG_ERR_OVERFLOW);
+        sum = kInf - 1u;
+      }
+      nd[q] = sum;
+      u[q] = e.x;
+      cur[q] = act[q] ? Dg_g[(size_t)e.x << LG] : 0u;
     }
 #pragma unroll
     for (int q = 0; q < kGUnroll; ++q) {
       const bool imp = act[q] && nd[q] < cur[q];
-      relaxed += act[q] ? 1ull : 0ull;
-      if (imp) atomicMin(Dg + ((size_t)u[q] << a.glog2) + (size_t)g, nd[q]);
+      relaxed += act[q] ? 1u : 0u;
+      if (imp) atomicMin(Dg_g + ((size_t)u[q] << LG), nd[q]);
       const unsigned im = __ballot_sync(kFull, imp);
-      const unsigned mine = (im >> (h * G_)) & gmask;
-      if (mine != 0u && g == 0) {
-        atomicOr(pend_g + u[q], mine);
-        dirty_g[u[q] >> slog2] = 1u;
-        improved += (unsigned long long)__popc(mine);
-      }
-      if (gbest_n != nullptr) {
-        // smallest new value of the group, for the next round's window
-        const uint32_t mn = __reduce_min_sync(kFull, imp ? nd[q] : kInf);
-        if (mn != kInf && (threadIdx.x & 31) == 0) atomicMin(gbest_n, mn);
+      if (im != 0u) {  // warp-uniform: most steps improve nothing
+        const unsigned mine = (im >> (h * GQ)) & GM;
+        if (mine != 0u && g == 0) {
+          atomicOr(pend_g + u[q], mine);
+          dirty_g[u[q] >> slog2] = 1u;
+          improved += (uint32_t)__popc(mine);
+        }
+        if (gbest_n != nullptr) {
+          // smallest new value of the group, for the next round's window
+          const uint32_t mn = __reduce_min_sync(kFull, imp ? nd[q] : kInf);
+          if (mn != kInf && (threadIdx.x & 31) == 0) atomicMin(gbest_n, mn);
+        }
       }
     }
   }
 }
 
-template <int QT>
+template <int QT, int GQ>
 __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
   extern __shared__ __align__(16) uint32_t g_smem[];
   __shared__ __align__(8) uint64_t s_full[2], s_empty[2], s_tma[2];
@@ -140,22 +148,26 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
   const bool producer = wid == kGCons;
   const DevGraph &G = a.g;
   const int S = G.S;
-  const int Gq = a.G;
-  const int g = lane & (Gq - 1);     // query of the group held by this lane
-  const int h = lane >> a.glog2;     // arc slot of this lane
-  const int SL = 32 >> a.glog2;      // arc slots per warp
+  constexpr int Gq = GQ;
+  constexpr int LG = ilog2c(GQ);
+  constexpr int SL = 32 / GQ;       // arc slots per warp
+  const int g = lane & (Gq - 1);    // query of the group held by this lane
+  const int h = lane >> LG;         // arc slot of this lane
   const size_t iw = group_item_words(S);
   // item buffer k: rp [S + 4], pm [S], vid [S], pre [S + 4]
   auto buf_rp = [&](uint32_t k) { return g_smem + k * iw; };
   auto buf_pm = [&](uint32_t k) { return g_smem + k * iw + (S + 4); };
   auto buf_vid = [&](uint32_t k) { return g_smem + k * iw + (S + 4) + S; };
   auto buf_pre = [&](uint32_t k) { return g_smem + k * iw + (S + 4) + 2 * S; };
-  uint32_t *sdv = g_smem + 2 * iw + (size_t)(producer ? 0 : wid) * 32u * (uint32_t)Gq;  // [32][G]
+  // per consumer warp: the step's arcs (uint4[32]) and the batch's source values ([32][G])
+  uint4 *sarc = reinterpret_cast<uint4 *>(g_smem + 2 * iw) + (size_t)(producer ? 0 : wid) * 32u;
+  uint32_t *sdv = g_smem + 2 * iw + (size_t)kGCons * 128u + (size_t)(producer ? 0 : wid) * 32u * (uint32_t)Gq;
   Ctrl *c = a.ctrl;
   unsigned gen = *reinterpret_cast<volatile unsigned *>(&c->bar_gen);
   uint32_t it_base = 0;   // items this block has gone through (both buffers), the same in every warp
   uint32_t tma_bits = 0;  // producer: phase parity of s_tma[0] (bit 0) and s_tma[1] (bit 1)
   unsigned long long n_relaxed = 0, n_improved = 0, n_visits = 0, n_arcs = 0;
+  uint32_t r32 = 0, i32 = 0;  // per-batch counters, folded into the 64-bit ones after each batch
   uint64_t t_prev = (blockIdx.x == 0 && threadIdx.x == 0) ? global_ns() : 0ull;
   unsigned long long ph[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
 #define FG_GPHASE(k)                                            \
@@ -378,23 +390,40 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
           break;
         }
         uint32_t *Dg = a.D + (size_t)d.grp * row * (size_t)Gq;
+        uint32_t *Dg_g = Dg + g;
         uint32_t *pend_g = pend_n + (size_t)d.grp * row;
         uint32_t *dirty_g = dirty_n + (size_t)d.grp * G.nparts;
         uint32_t *gb_n = a.gbest ? a.gbest + (size_t)nxt * a.ngroups + d.grp : nullptr;
+        // Steps of 32 arcs: lane l computes arc l of the next step and issues its
+        // loads before the current step is relaxed, then stages it in sarc.
+        auto run = [&](uint32_t nsteps, auto make, const uint32_t *sdv_g, uint32_t dv_own) {
+          uint4 nx = make(0u);
+          for (uint32_t i = 0; i < nsteps; ++i) {
+            sarc[lane] = nx;
+            __syncwarp();
+            if (i + 1u < nsteps) nx = make(i + 1u);
+            g_step<QT, GQ>(a, sarc, sdv_g, dv_own, Dg_g, pend_g, dirty_g, gb_n, g, h, r32, i32);
+            __syncwarp();  // sarc is rewritten by the next step
+          }
+        };
         if (d.kind == kItemHub) {
           uint32_t dv = kInf;
-          if (((d.m >> g) & 1u) != 0u) dv = __ldcg(Dg + ((size_t)d.pv << a.glog2) + (size_t)g);
+          if (((d.m >> g) & 1u) != 0u) dv = __ldcg(Dg_g + ((size_t)d.pv << LG));
           for (;;) {
-            uint32_t s = 0;
-            if (lane == 0) s = atomicAdd(&s_desc[k].next, 1u);
-            s = __shfl_sync(kFull, s, 0);
-            if (s >= d.n) break;
-            const uint32_t e = d.eb + s * 32u + (uint32_t)lane;
-            const bool has = e < d.ee;
-            const uint32_t au = has ? __ldg(G.adj + e) : 0u;
-            const uint32_t aw = (has && QT != Q_BFS && G.wt != nullptr) ? __ldg(G.wt + e) : 1u;
-            n_arcs += has ? 1ull : 0ull;
-            g_step<QT>(a, au, aw, 0u, has, nullptr, dv, Dg, pend_g, dirty_g, gb_n, g, h, SL, n_relaxed, n_improved);
+            uint32_t s0 = 0;
+            if (lane == 0) s0 = atomicAdd(&s_desc[k].next, 4u);  // four steps of 32 arcs at a time
+            s0 = __shfl_sync(kFull, s0, 0);
+            if (s0 >= d.n) break;
+            const uint32_t ns = d.n - s0 < 4u ? d.n - s0 : 4u;
+            auto make = [&](uint32_t i) {
+              const uint32_t e = d.eb + (s0 + i) * 32u + (uint32_t)lane;
+              const bool has = e < d.ee;
+              n_arcs += has ? 1ull : 0ull;
+              return make_uint4(has ? __ldg(G.adj + e) : 0u,
+                                (has && QT != Q_BFS && G.wt != nullptr) ? __ldg(G.wt + e) : 1u,
+                                has ? 0u : kNoArc, 0u);
+            };
+            run(ns, make, nullptr, dv);
           }
         } else {
           const uint32_t base = d.pv << G.slog2;
@@ -422,41 +451,48 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
             // L of sdv holds vertex L's values of the group, kInf where not
             // pending. Under a window, values at or beyond the group's bound
             // stay pending for a later round (Delta-stepping across rounds).
+#pragma unroll 4
             for (int L0 = 0; L0 < 32; L0 += SL) {
               const int L = L0 + h;
               const uint32_t vL = __shfl_sync(kFull, li, L);
               const uint32_t mL = __shfl_sync(kFull, m, L);
               uint32_t dd = kInf;
-              if (((mL >> g) & 1u) != 0u) dd = __ldcg(Dg + ((size_t)(base + vL) << a.glog2) + (size_t)g);
-              const bool def = dd != kInf && dd >= bound;
-              const unsigned dm = __ballot_sync(kFull, def);
-              const unsigned gmask = Gq == 32 ? 0xFFFFFFFFu : ((1u << Gq) - 1u);
-              const unsigned mine = (dm >> (h * Gq)) & gmask;
-              if (mine != 0u && g == 0) {
-                atomicOr(pend_g + base + vL, mine);
-                dirty_g[d.pv] = 1u;
+              if (((mL >> g) & 1u) != 0u) dd = __ldcg(Dg_g + ((size_t)(base + vL) << LG));
+              if (bound != kInf) {  // block-uniform
+                const bool def = dd != kInf && dd >= bound;
+                const unsigned dm = __ballot_sync(kFull, def);
+                const unsigned mine = (dm >> (h * Gq)) & (Gq == 32 ? 0xFFFFFFFFu : ((1u << Gq) - 1u));
+                if (mine != 0u && g == 0) {
+                  atomicOr(pend_g + base + vL, mine);
+                  dirty_g[d.pv] = 1u;
+                }
+                if (gb_n != nullptr) {
+                  const uint32_t mn = __reduce_min_sync(kFull, def ? dd : kInf);
+                  if (mn != kInf && lane == 0) atomicMin(gb_n, mn);
+                }
+                if (def) dd = kInf;
               }
-              if (gb_n != nullptr) {
-                const uint32_t mn = __reduce_min_sync(kFull, def ? dd : kInf);
-                if (mn != kInf && lane == 0) atomicMin(gb_n, mn);
-              }
-              sdv[(L << a.glog2) + g] = def ? kInf : dd;
+              sdv[(L << LG) + g] = dd;
             }
             __syncwarp();
-            for (uint32_t t0 = 0; t0 < tot; t0 += 32u) {
-              const uint32_t t = t0 + (uint32_t)lane;
+            auto make = [&](uint32_t i) {
+              const uint32_t t = i * 32u + (uint32_t)lane;
               const bool has = t < tot;
               const int L = owner_lane(exd, has ? t : 0u);
               const uint32_t eL = __shfl_sync(kFull, a0, L) + (t - __shfl_sync(kFull, exd, L));
-              const uint32_t au = has ? __ldg(G.adj + eL) : 0u;
-              const uint32_t aw = (has && QT != Q_BFS && G.wt != nullptr) ? __ldg(G.wt + eL) : 1u;
               n_arcs += has ? 1ull : 0ull;
-              g_step<QT>(a, au, aw, (uint32_t)L, has, sdv, kInf, Dg, pend_g, dirty_g, gb_n, g, h, SL, n_relaxed,
-                         n_improved);
-            }
+              return make_uint4(has ? __ldg(G.adj + eL) : 0u,
+                                (has && QT != Q_BFS && G.wt != nullptr) ? __ldg(G.wt + eL) : 1u,
+                                has ? (uint32_t)L : kNoArc, 0u);
+            };
+            run((tot + 31u) / 32u, make, sdv + g, kInf);
             __syncwarp();  // sdv is rewritten by the next batch
           }
         }
+        n_relaxed += r32;
+        n_improved += i32;
+        r32 = 0u;
+        i32 = 0u;
         __syncwarp();
         if (lane == 0) mbar_arrive(&s_empty[k]);  // this warp is done with buffer k
       }
@@ -508,8 +544,15 @@ __global__ void __launch_bounds__(256) group_out_kernel(const uint32_t *D, uint3
   }
 }
 
-static const void *group_fn(int qtype) {
-  return qtype == Q_BFS ? (const void *)group_kernel<Q_BFS> : (const void *)group_kernel<Q_SSSP>;
+static const void *group_fn(int qtype, int G) {
+  if (qtype == Q_BFS) {
+    if (G == 8) return (const void *)group_kernel<Q_BFS, 8>;
+    if (G == 16) return (const void *)group_kernel<Q_BFS, 16>;
+    return (const void *)group_kernel<Q_BFS, 32>;
+  }
+  if (G == 8) return (const void *)group_kernel<Q_SSSP, 8>;
+  if (G == 16) return (const void *)group_kernel<Q_SSSP, 16>;
+  return (const void *)group_kernel<Q_SSSP, 32>;
 }
 
 cudaError_t group_grid_size(int S, int G, int *blocks, int *threads, size_t *smem) {
@@ -518,7 +561,7 @@ cudaError_t group_grid_size(int S, int G, int *blocks, int *threads, size_t *sme
   int best = 1 << 30, dev = 0, sms = 0;
   cudaError_t e;
   for (int qt = 0; qt < 2; ++qt) {
-    const void *fn = group_fn(qt);
+    const void *fn = group_fn(qt, G);
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem)) != cudaSuccess)
       return e;
     int per_sm = 0;
@@ -536,7 +579,7 @@ cudaError_t group_grid_size(int S, int G, int *blocks, int *threads, size_t *sme
 cudaError_t launch_group(const GroupArgs &a, int blocks, int threads, size_t smem, cudaStream_t s) {
   GroupArgs copy = a;
   void *args[] = {(void *)&copy};
-  return cudaLaunchCooperativeKernel(group_fn(a.qtype), dim3(blocks), dim3(threads), args, smem, s);
+  return cudaLaunchCooperativeKernel(group_fn(a.qtype, a.G), dim3(blocks), dim3(threads), args, smem, s);
 }
 
 cudaError_t launch_group_out(const GroupArgs &a, uint32_t *out, cudaStream_t s) {
