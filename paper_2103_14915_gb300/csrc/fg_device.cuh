@@ -200,6 +200,11 @@ __device__ __forceinline__ void cp_async16_cg(void *smem_dst, const void *gmem_s
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem_dst)), "l"(gmem_src) : "memory");
 }
 
+// Ask L2 to fetch the line holding p (no register, no completion to wait for).
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
 template <int N>

@@ -99,7 +99,7 @@ __device__ __forceinline__ void g_step(const GroupArgs &a, const uint4 *sarc, co
   const int slog2 = a.g.slog2;
 #pragma unroll
   for (int j0 = 0; j0 < 32; j0 += SL * kGUnroll) {
-    uint32_t u[kGUnroll], nd[kGUnroll], cur[kGUnroll];
+    uint32_t nd[kGUnroll], cur[kGUnroll];
     bool act[kGUnroll];
 #pragma unroll
     for (int q = 0; q < kGUnroll; ++q) {
@@ -113,20 +113,20 @@ __device__ __forceinline__ void g_step(const GroupArgs &a, const uint4 *sarc, co
         sum = kInf - 1u;
       }
       nd[q] = sum;
-      u[q] = e.x;
       cur[q] = act[q] ? Dg_g[(size_t)e.x << LG] : 0u;
     }
 #pragma unroll
     for (int q = 0; q < kGUnroll; ++q) {
       const bool imp = act[q] && nd[q] < cur[q];
       relaxed += act[q] ? 1u : 0u;
-      if (imp) atomicMin(Dg_g + ((size_t)u[q] << LG), nd[q]);
+      const uint32_t uq = sarc[j0 + q * SL + h].x;  // read again rather than held in a register
+      if (imp) atomicMin(Dg_g + ((size_t)uq << LG), nd[q]);
       const unsigned im = __ballot_sync(kFull, imp);
       if (im != 0u) {  // warp-uniform: most steps improve nothing
         const unsigned mine = (im >> (h * GQ)) & GM;
         if (mine != 0u && g == 0) {
-          atomicOr(pend_g + u[q], mine);
-          dirty_g[u[q] >> slog2] = 1u;
+          atomicOr(pend_g + uq, mine);
+          dirty_g[uq >> slog2] = 1u;
           improved += (uint32_t)__popc(mine);
         }
         if (gbest_n != nullptr) {
@@ -394,16 +394,25 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
         uint32_t *pend_g = pend_n + (size_t)d.grp * row;
         uint32_t *dirty_g = dirty_n + (size_t)d.grp * G.nparts;
         uint32_t *gb_n = a.gbest ? a.gbest + (size_t)nxt * a.ngroups + d.grp : nullptr;
-        // Steps of 32 arcs: lane l computes arc l of the next step and issues its
-        // loads before the current step is relaxed, then stages it in sarc.
+        // Steps of 32 arcs, lane l holding arc l. Two steps ahead of the one
+        // being relaxed, a lane loads its arc (target, weight); one step ahead,
+        // it asks L2 for the arc's target line (prefetch.global.L2), so the
+        // relaxation's loads of target values find their lines on chip
+        // without holding registers while they travel.
         auto run = [&](uint32_t nsteps, auto make, const uint32_t *sdv_g, uint32_t dv_own) {
-          uint4 nx = make(0u);
+          const uint4 none = make_uint4(0u, 1u, kNoArc, 0u);
+          uint4 a0 = make(0u);
+          uint4 a1 = nsteps > 1u ? make(1u) : none;
+          if (a0.z != kNoArc) prefetch_l2(Dg + ((size_t)a0.x << LG));
           for (uint32_t i = 0; i < nsteps; ++i) {
-            sarc[lane] = nx;
+            sarc[lane] = a0;
             __syncwarp();
-            if (i + 1u < nsteps) nx = make(i + 1u);
+            if (a1.z != kNoArc) prefetch_l2(Dg + ((size_t)a1.x << LG));
+            const uint4 a2 = i + 2u < nsteps ? make(i + 2u) : none;
             g_step<QT, GQ>(a, sarc, sdv_g, dv_own, Dg_g, pend_g, dirty_g, gb_n, g, h, r32, i32);
             __syncwarp();  // sarc is rewritten by the next step
+            a0 = a1;
+            a1 = a2;
           }
         };
         if (d.kind == kItemHub) {
