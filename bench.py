@@ -68,6 +68,7 @@ def parse():
                     help="plumbing tests only: a smaller R-MAT of the same recipe instead of scale 24")
     ap.add_argument("--no-ppr-check", action="store_true", help="skip the R-MAT s22 PPR error record")
     ap.add_argument("--no-grid-extra", action="store_true", help="skip the grid workload extra key")
+    ap.add_argument("--no-serving-extra", action="store_true", help="skip the R-MAT s25 serving extra key")
     ap.add_argument("--cpu-sources", type=int, default=0,
                     help="sources of the CPU oracle sample (default: one per host core, at most 16)")
     ap.add_argument("--opts-bfs", default="", help="JSON overrides of fg_opts for the BFS batches")
@@ -402,7 +403,8 @@ def run_serving(args):
         for kind in (fg.FG_QUERY_SSSP, fg.FG_QUERY_BFS):
             st, best, _ = fg.fg_tune_opts(h, kind, sample, 64)
             fg.check(st)
-            opts[kind] = {k: int(getattr(best, k)) for k in ("sched", "sched_window", "delta", "threads_per_vertex")}
+            opts[kind] = {k: int(getattr(best, k)) for k in ("group", "sched", "sched_window", "delta",
+                                                             "threads_per_vertex")}
         for lam in [float(x) for x in args.serve_lambdas.split(",") if x]:
             runs.append(serve_stream(fg, h, g, lam, args.serve_requests, seed=int(lam), lanes=4, max_batch=256,
                                      kinds=(0, 1, 2), alpha=0.15, eps=1e-6, opts=opts))
@@ -1110,6 +1112,26 @@ def grid_extra(fg, inputs, dev, stream):
         fg.fg_graph_destroy(h)
 
 
+def serving_extra(fg, inputs, requests=300, lambdas=(2000.0, 50000.0)):
+    """The serving workload (directed R-MAT s25, edge factor 24): Poisson streams of mixed
+    SSSP / BFS / PPR(alpha 0.15, eps 1e-6) requests through fg_server_*, at the lowest and
+    highest arrival rates of the workload; both are above what the loop sustains, so the
+    runs measure the saturated throughput and the latency a queue of that depth gives."""
+    g = inputs.workload_graph("rmat25_serving")
+    st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, fg.fg_default_graph_opts())
+    fg.check(st)
+    try:
+        opts = {0: {"group": 32}, 1: {"group": 32}}
+        runs = [serve_stream(fg, h, g, lam, requests, seed=int(lam), lanes=4, max_batch=64, kinds=(0, 1, 2),
+                             alpha=0.15, eps=1e-6, opts=opts) for lam in lambdas]
+    finally:
+        fg.fg_graph_destroy(h)
+    return {"workload": "rmat25_serving", "graph": "directed R-MAT scale 25, edge factor 24, weights [1,255]",
+            "mix": "1/3 SSSP, 1/3 BFS, 1/3 PPR(alpha=0.15, eps=1e-6)", "requests_per_rate": requests,
+            "sustained_qps": max(r["throughput_qps"] for r in runs), "opts": {"sssp": opts[0], "bfs": opts[1]},
+            "runs": runs}
+
+
 def run_rmat24(args):
     """The main line: SSSP batches of B sources on R-MAT scale 24 (see the module docstring)."""
     import torch
@@ -1309,6 +1331,8 @@ def run_rmat24(args):
                 result["grid1024_bfs_sssp"] = grid_extra(fg, inputs, dev, stream)
             if not args.no_ppr_check:
                 result["ppr_rmat22"] = ppr_error_record(fg, inputs, oracle, dev)
+            if not args.no_serving_extra:
+                result["serving_rmat25"] = serving_extra(fg, inputs)
     if h is not None:
         fg.fg_graph_destroy(h)
     if rank == 0:
