@@ -245,14 +245,15 @@ def engine_traffic():
 
 
 def serve_stream(fg, h, g, lam, n_req, seed, lanes, max_batch, kinds=(0, 1, 2), alpha=0.15, eps=1e-6,
-                 opts=None):
+                 opts=None, continuous=0, slots=128):
     """Poisson stream of single-source requests through the serving loop (fg_server_*).
 
     Request i arrives at a seeded exponential-gap time, with a kind drawn
     uniformly from `kinds` and a seeded-uniform source. The host loop submits
     requests as their arrival time passes, polls, and releases completed ones.
     Latency = completion seen by fg_server_poll - scheduled arrival (host
-    monotonic clock, the server's steady clock).
+    monotonic clock, the server's steady clock). continuous=1 runs SSSP and
+    BFS with slot-level batching (`slots` query lanes per kind).
     """
     from paper_2103_14915_gb300 import inputs
     rng = np.random.default_rng(seed)
@@ -261,7 +262,8 @@ def serve_stream(fg, h, g, lam, n_req, seed, lanes, max_batch, kinds=(0, 1, 2), 
     kind = rng.choice(np.asarray(kinds, dtype=np.int32), n_req)
     pool = inputs.sources_uniform(g, min(n_req, 65536), seed + 1)
     src = pool[rng.integers(0, len(pool), n_req)]
-    so = fg.fg_default_server_opts(lanes=lanes, max_batch=max_batch, alpha=alpha, eps=eps)
+    so = fg.fg_default_server_opts(lanes=lanes, max_batch=max_batch, alpha=alpha, eps=eps,
+                                   continuous=continuous, slots=slots)
     for k, o in (opts or {}).items():
         for key, v in o.items():
             setattr(so.opts[k], key, v)
@@ -304,7 +306,8 @@ def serve_stream(fg, h, g, lam, n_req, seed, lanes, max_batch, kinds=(0, 1, 2), 
             "throughput_qps": n_req / ((t_end - t0) / 1e9 - 0.0),
             "p50_ms": float(np.percentile(allv, 50)), "p99_ms": float(np.percentile(allv, 99)),
             "per_kind_p99_ms": {names[k]: float(np.percentile(v, 99)) for k, v in lat.items() if v},
-            "mean_batch": float(np.mean(batch)), "lanes": lanes, "max_batch": max_batch}
+            "mean_batch": float(np.mean(batch)), "lanes": lanes, "max_batch": max_batch,
+            "mode": "slots" if continuous else "batches", **({"slots": slots} if continuous else {})}
 
 
 def bench_graph(args):
@@ -408,6 +411,10 @@ def run_serving(args):
         for lam in [float(x) for x in args.serve_lambdas.split(",") if x]:
             runs.append(serve_stream(fg, h, g, lam, args.serve_requests, seed=int(lam), lanes=4, max_batch=256,
                                      kinds=(0, 1, 2), alpha=0.15, eps=1e-6, opts=opts))
+            # slot-level batching of SSSP and BFS (group engine, 32 lanes per group)
+            sopts = {k: dict(v, group=32) for k, v in opts.items()}
+            runs.append(serve_stream(fg, h, g, lam, args.serve_requests, seed=int(lam), lanes=2, max_batch=256,
+                                     kinds=(0, 1, 2), alpha=0.15, eps=1e-6, opts=sopts, continuous=1, slots=128))
     finally:
         fg.fg_graph_destroy(h)
     best = max(r["throughput_qps"] for r in runs)
@@ -416,7 +423,10 @@ def run_serving(args):
                       "config": {"workload": name, "graph": "directed R-MAT scale 25, edge factor 24, weights [1,255]",
                                  "mix": "1/3 SSSP, 1/3 BFS, 1/3 PPR(alpha=0.15, eps=1e-6)",
                                  "requests_per_rate": args.serve_requests},
-                      "sustained_qps": best, "opts": {"sssp": opts[0], "bfs": opts[1]}, "runs": runs}), flush=True)
+                      "sustained_qps": best,
+                      "sustained_qps_by_mode": {m: max(r["throughput_qps"] for r in runs if r["mode"] == m)
+                                                for m in ("batches", "slots")},
+                      "opts": {"sssp": opts[0], "bfs": opts[1]}, "runs": runs}), flush=True)
 
 
 def run_ablation(args):
@@ -1124,12 +1134,18 @@ def serving_extra(fg, inputs, requests=300, lambdas=(2000.0, 50000.0)):
         opts = {0: {"group": 32}, 1: {"group": 32}}
         runs = [serve_stream(fg, h, g, lam, requests, seed=int(lam), lanes=4, max_batch=64, kinds=(0, 1, 2),
                              alpha=0.15, eps=1e-6, opts=opts) for lam in lambdas]
+        # slot-level batching: SSSP and BFS join running launches lane by lane,
+        # PPR keeps two batch lanes
+        runs += [serve_stream(fg, h, g, lam, requests, seed=int(lam), lanes=2, max_batch=64, kinds=(0, 1, 2),
+                              alpha=0.15, eps=1e-6, opts=opts, continuous=1, slots=128) for lam in lambdas]
     finally:
         fg.fg_graph_destroy(h)
     return {"workload": "rmat25_serving", "graph": "directed R-MAT scale 25, edge factor 24, weights [1,255]",
             "mix": "1/3 SSSP, 1/3 BFS, 1/3 PPR(alpha=0.15, eps=1e-6)", "requests_per_rate": requests,
-            "sustained_qps": max(r["throughput_qps"] for r in runs), "opts": {"sssp": opts[0], "bfs": opts[1]},
-            "runs": runs}
+            "sustained_qps": max(r["throughput_qps"] for r in runs),
+            "sustained_qps_by_mode": {m: max(r["throughput_qps"] for r in runs if r["mode"] == m)
+                                      for m in ("batches", "slots")},
+            "opts": {"sssp": opts[0], "bfs": opts[1]}, "runs": runs}
 
 
 def run_rmat24(args):

@@ -284,6 +284,20 @@ fg_status fg_tune_opts_ex(fg_graph *g, int32_t kind, const int32_t *src, int32_t
  * fg_ppr_batch. The graph must outlive the server. Calls on one server are
  * serialised by the server's lock; fg_server_submit may be called from any
  * thread.
+ *
+ * Slot-level batching (continuous = 1): SSSP and BFS requests no longer wait
+ * for a batch. Each of the two kinds has `slots` query lanes of the group
+ * engine with their own state and result rows, and a mailbox in mapped host
+ * memory. fg_server_poll writes a waiting request into a free slot; a running
+ * launch admits it at its next round boundary, runs it alongside the queries
+ * already in flight, and posts its completion as soon as that query has no
+ * pending work left, whatever the other lanes are doing. A launch ends when
+ * it holds no query and finds no new request; fg_server_poll starts one when a
+ * slot holds a request. A slot is free again when its request is released.
+ * The two slot lanes take half of hbm_budget (slots lowered to fit); PPR
+ * requests still run in batches on the lanes, and the resident grid is
+ * shared by lanes + 2 launches unless full_grid. The same results as batch
+ * mode; batch_size reports the kind's slot count.
  */
 typedef struct fg_server fg_server;
 
@@ -295,6 +309,9 @@ typedef struct {
     float alpha, eps;       /* PPR parameters of every PPR request (default 0.15, 1e-6) */
     int64_t hbm_budget;     /* device bytes for all lanes' batches; 0 (default) = 60% of free memory */
     fg_opts opts[3];        /* engine options per kind (SSSP, BFS, PPR); struct_size 0 = defaults */
+    int32_t continuous;     /* 1: slot-level batching of SSSP and BFS (below); 0 (default): batches on lanes */
+    int32_t slots;          /* continuous: query slots per kind, a multiple of the group size (opts[0].group if
+                               8, 16 or 32, else 32); default 128, lowered to fit half of hbm_budget */
 } fg_server_opts;
 
 typedef struct {

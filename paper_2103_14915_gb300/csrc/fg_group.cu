@@ -93,7 +93,8 @@ constexpr uint32_t kNoArc = 0xFFFFFFFFu;
 template <int QT, int GQ>
 __device__ __forceinline__ void g_step(const GroupArgs &a, const uint4 *sarc, const uint32_t *sdv_g,
                                        uint32_t dv_own, uint32_t *Dg_g, uint32_t *pend_g, uint32_t *dirty_g,
-                                       uint32_t *gbest_n, int g, int h, uint32_t &relaxed, uint32_t &improved) {
+                                       uint32_t *gbest_n, int g, int h, uint32_t &relaxed, uint32_t &improved,
+                                       uint32_t &lanes_marked) {
   constexpr int LG = ilog2c(GQ), SL = 32 / GQ;
   constexpr unsigned GM = GQ == 32 ? 0xFFFFFFFFu : ((1u << GQ) - 1u);
   const int slog2 = a.g.slog2;
@@ -128,6 +129,7 @@ __device__ __forceinline__ void g_step(const GroupArgs &a, const uint4 *sarc, co
           atomicOr(pend_g + uq, mine);
           dirty_g[uq >> slog2] = 1u;
           improved += (uint32_t)__popc(mine);
+          lanes_marked |= mine;
         }
         if (gbest_n != nullptr) {
           // smallest new value of the group, for the next round's window
@@ -194,8 +196,9 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
   const uint64_t tid = (uint64_t)blockIdx.x * kGThreads + threadIdx.x, nthr = (uint64_t)gridDim.x * kGThreads;
   const size_t row = (size_t)a.npad;  // vertices per group row
 
-  // ---- K0: state and masks (InitBuffers, first half) ----
-  {
+  // ---- K0: state and masks (InitBuffers, first half); in serve mode only on
+  //      the first launch on the state (later launches resume it) ----
+  if (a.box == nullptr || a.init != 0u) {
     const uint64_t dwords = (uint64_t)a.ngroups * (uint64_t)a.npad * (uint64_t)Gq;
     for (uint64_t i = tid; i < dwords / 4u; i += nthr)
       reinterpret_cast<uint4 *>(a.D)[i] = make_uint4(kInf, kInf, kInf, kInf);
@@ -204,12 +207,15 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
     for (uint64_t i = tid; i < 2ull * K; i += nthr) a.dirty[i] = 0u;
     if (a.gbest)
       for (uint64_t i = tid; i < 2ull * (uint64_t)a.ngroups; i += nthr) a.gbest[i] = kInf;
+    if (a.gact)
+      for (uint64_t i = tid; i < 2ull * (uint64_t)a.ngroups; i += nthr) a.gact[i] = 0u;
   }
   if (!grid_barrier(c, gen, a.watchdog_ns)) goto done;
   FG_GPHASE(0);
 
-  // ---- INIT: each query's source gets value 0 and is pending in round 0 ----
-  for (uint64_t q = tid; q < (uint64_t)a.nq; q += nthr) {
+  // ---- INIT: each query's source gets value 0 and is pending in round 0
+  //      (serve mode: sources come through the mailbox instead) ----
+  for (uint64_t q = tid; a.box == nullptr && q < (uint64_t)a.nq; q += nthr) {
     const int32_t s = a.src[q];
     if (s < 0 || s >= G.n) {
       raise_status(c, FG_ERR_INVALID_ARG, kSiteSource);
@@ -225,7 +231,7 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
   if (!grid_barrier(c, gen, a.watchdog_ns)) goto done;
   FG_GPHASE(1);
 
-  for (uint32_t round = 0;; ++round) {
+  for (uint32_t round = a.round0;; ++round) {
     const uint32_t cur = round & 1u, nxt = cur ^ 1u;
     uint32_t *pend_c = a.pend + (size_t)cur * (size_t)a.ngroups * row;
     uint32_t *pend_n = a.pend + (size_t)nxt * (size_t)a.ngroups * row;
@@ -240,6 +246,8 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
       }
       if (a.gbest)
         for (uint64_t i = tid; i < (uint64_t)a.ngroups; i += nthr) a.gbest[(size_t)nxt * a.ngroups + i] = kInf;
+      if (a.gact)
+        for (uint64_t i = tid; i < (uint64_t)a.ngroups; i += nthr) a.gact[(size_t)nxt * a.ngroups + i] = 0u;
       const uint64_t HK = (uint64_t)a.nhubs * (uint64_t)a.ngroups;
       for (uint64_t k = tid; k < HK; k += nthr) {
         const uint32_t grp = (uint32_t)(k / (uint64_t)a.nhubs), hi = (uint32_t)(k % (uint64_t)a.nhubs);
@@ -275,8 +283,77 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
     FG_GPHASE(2);
     const uint32_t n_hub = umin64(*reinterpret_cast<volatile unsigned *>(&c->g_hub_items[cur]), a.hub_cap);
     const uint32_t n_reg = *reinterpret_cast<volatile unsigned *>(&c->g_items[cur]);
-    if (n_hub + n_reg == 0u) break;
-    if (round >= a.max_rounds) {
+    if (a.box != nullptr) {
+      // ---- serve mode: RETIRE lanes whose query has no pending work left, then
+      //      ADMIT the mailbox's new requests into free lanes (next round) ----
+      const uint32_t *gact_c = a.gact + (size_t)cur * a.ngroups;
+      for (uint32_t grp = 0; grp < (uint32_t)a.ngroups; ++grp) {
+        const uint32_t f = __ldcg(a.occ + grp) & ~__ldcg(gact_c + grp);  // the same in every block
+        if (f == 0u) continue;
+        uint32_t *Dg = a.D + (size_t)grp * row * (size_t)Gq;
+        for (uint64_t v = tid; v < (uint64_t)G.n; v += nthr) {
+          const uint64_t o = G.orig ? (uint64_t)G.orig[v] : v;
+          uint32_t bits = f;
+          while (bits != 0u) {
+            const int gg = __ffs(bits) - 1;
+            bits &= bits - 1u;
+            uint32_t *pv = Dg + (v << LG) + (uint64_t)gg;
+            a.res[((uint64_t)grp * (uint64_t)Gq + (uint64_t)gg) * (uint64_t)G.n + o] = __ldcg(pv);
+            *pv = kInf;  // the lane starts over for its next request
+          }
+        }
+      }
+      if (!grid_barrier(c, gen, a.watchdog_ns)) goto done;
+      if (blockIdx.x == 0 && wid == 0) {
+        const uint32_t slots = (uint32_t)a.ngroups * (uint32_t)Gq;
+        uint32_t admitted = 0;
+        for (uint32_t sl = (uint32_t)lane; sl < slots; sl += 32u) {
+          const uint32_t grp = sl >> LG, bit = 1u << (sl & (uint32_t)(Gq - 1));
+          ServeSlot *bx = a.box->slot + sl;
+          if ((__ldcg(a.occ + grp) & ~__ldcg(gact_c + grp) & bit) != 0u) {
+            // the row is complete in res (written before the barrier): the
+            // fence orders it and the status before the completion record
+            st_volatile_sys(&bx->status, (int)FG_OK);
+            __threadfence_system();
+            st_volatile_sys(&bx->done_seq, a.seen[sl]);
+            atomicAnd(a.occ + grp, ~bit);
+          }
+          if ((__ldcg(a.occ + grp) & bit) != 0u) continue;
+          const uint32_t seq = ld_volatile_sys(&bx->seq);
+          if (seq == a.seen[sl]) continue;
+          fence_acq_rel_sys();
+          const int32_t src = (int32_t)ld_volatile_sys(reinterpret_cast<uint32_t *>(&bx->src));
+          a.seen[sl] = seq;
+          st_volatile_sys(&bx->ack, seq);
+          if (src < 0 || src >= G.n) {  // rejected at once: the row is not written
+            st_volatile_sys(&bx->status, (int)FG_ERR_INVALID_ARG);
+            __threadfence_system();
+            st_volatile_sys(&bx->done_seq, seq);
+            continue;
+          }
+          const uint32_t v = G.intl ? (uint32_t)G.intl[src] : (uint32_t)src;
+          a.D[((size_t)grp * row + v) * (size_t)Gq + (sl & (uint32_t)(Gq - 1))] = 0u;
+          atomicOr(pend_n + (size_t)grp * row + v, bit);
+          dirty_n[(size_t)grp * G.nparts + (v >> G.slog2)] = 1u;
+          atomicOr(a.gact + (size_t)nxt * a.ngroups + grp, bit);
+          atomicOr(a.occ + grp, bit);
+          if (a.gbest) atomicMin(a.gbest + (size_t)nxt * a.ngroups + grp, 0u);
+          ++admitted;
+        }
+        __syncwarp();
+        uint32_t busy = 0;
+        for (uint32_t grp = (uint32_t)lane; grp < (uint32_t)a.ngroups; grp += 32u) busy |= __ldcg(a.occ + grp);
+        busy = __reduce_or_sync(kFull, busy);
+        admitted = __reduce_add_sync(kFull, admitted);
+        // idle (nothing to process, no lane held) or told to stop: the launch
+        // ends; the host relaunches it when a request waits unacknowledged
+        const bool stop = ld_volatile_sys(&a.box->stop) != 0u;
+        if (lane == 0) c->g_exit = (stop || (n_hub + n_reg == 0u && busy == 0u && admitted == 0u)) ? 1u : 0u;
+      }
+    } else if (n_hub + n_reg == 0u) {
+      break;
+    }
+    if (a.box == nullptr && round >= a.max_rounds) {
       if (threadIdx.x == 0) raise_status(c, FG_ERR_TIMEOUT, kSiteRounds);
       break;
     }
@@ -391,6 +468,7 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
         }
         uint32_t *Dg = a.D + (size_t)d.grp * row * (size_t)Gq;
         uint32_t *Dg_g = Dg + g;
+        uint32_t gacc = 0u;  // lanes this warp marked pending for the next round (serve mode)
         uint32_t *pend_g = pend_n + (size_t)d.grp * row;
         uint32_t *dirty_g = dirty_n + (size_t)d.grp * G.nparts;
         uint32_t *gb_n = a.gbest ? a.gbest + (size_t)nxt * a.ngroups + d.grp : nullptr;
@@ -409,7 +487,7 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
             __syncwarp();
             if (a1.z != kNoArc) prefetch_l2(Dg + ((size_t)a1.x << LG));
             const uint4 a2 = i + 2u < nsteps ? make(i + 2u) : none;
-            g_step<QT, GQ>(a, sarc, sdv_g, dv_own, Dg_g, pend_g, dirty_g, gb_n, g, h, r32, i32);
+            g_step<QT, GQ>(a, sarc, sdv_g, dv_own, Dg_g, pend_g, dirty_g, gb_n, g, h, r32, i32, gacc);
             __syncwarp();  // sarc is rewritten by the next step
             a0 = a1;
             a1 = a2;
@@ -474,6 +552,7 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
                 if (mine != 0u && g == 0) {
                   atomicOr(pend_g + base + vL, mine);
                   dirty_g[d.pv] = 1u;
+                  gacc |= mine;
                 }
                 if (gb_n != nullptr) {
                   const uint32_t mn = __reduce_min_sync(kFull, def ? dd : kInf);
@@ -502,6 +581,10 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
         n_improved += i32;
         r32 = 0u;
         i32 = 0u;
+        if (a.gact != nullptr) {
+          gacc = __reduce_or_sync(kFull, gacc);
+          if (lane == 0 && gacc != 0u) atomicOr(a.gact + (size_t)nxt * a.ngroups + d.grp, gacc);
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(&s_empty[k]);  // this warp is done with buffer k
       }
@@ -509,6 +592,11 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
     }
     if (!grid_barrier(c, gen, a.watchdog_ns)) goto done;
     FG_GPHASE(5);
+    // serve mode: leave when idle or told to stop, or yield after max_rounds
+    // rounds with the state intact (the next launch resumes at round + 1)
+    if (a.box != nullptr &&
+        (*reinterpret_cast<volatile unsigned *>(&c->g_exit) != 0u || round + 1u - a.round0 >= a.max_rounds))
+      break;
   }
 done:
 #undef FG_GPHASE

@@ -50,6 +50,26 @@ struct Ctrl {
   unsigned int g_hub_items[2], g_items[2], g_next[2];
   unsigned long long arcs_read;  // graph arcs read (per query visit, or per group visit)
   unsigned int max_ops[2];       // largest buffer of the round, per round parity (max-operations scheduling)
+  unsigned int g_exit;           // group engine, serve mode: the launch ends after this round
+};
+
+// Serve mode of the group engine (continuous batching): a mailbox in mapped
+// host memory. The host writes a slot's source, then a new sequence number;
+// at a round boundary the running launch admits it into that query lane and
+// acknowledges it; when the lane's query has no pending work left, the launch
+// copies its row out and writes the sequence number to done_seq.
+struct ServeSlot {
+  int32_t src;        // host: original source id
+  uint32_t seq;       // host: a new value = a new request in this slot
+  uint32_t ack;       // device: the last sequence number admitted
+  uint32_t done_seq;  // device: the last sequence number completed (its row is in res)
+  int32_t status;     // device: fg_status of that request
+  uint32_t pad[3];
+};
+struct ServeBox {
+  uint32_t stop;      // host: leave at the next round boundary, work or not (the state is then refilled)
+  uint32_t pad[7];
+  ServeSlot slot[1];  // [slots]
 };
 
 struct EngineArgs {
@@ -114,6 +134,14 @@ struct GroupArgs {
   Ctrl *ctrl = nullptr;
   uint32_t max_rounds = 0;
   uint64_t watchdog_ns = 0;
+  // serve mode (continuous batching); off when box is null
+  ServeBox *box = nullptr;        // mapped host mailbox, ngroups * G slots (device address)
+  uint32_t *res = nullptr;        // [slots][n] result rows, original vertex order
+  uint32_t *occ = nullptr;        // [ngroups] lanes holding an admitted, unfinished query
+  uint32_t *seen = nullptr;       // [slots] sequence number of each slot's current request
+  uint32_t *gact = nullptr;       // [2][ngroups] lanes with pending work in the round of that parity
+  uint32_t init = 0;              // 1: first launch on this state: fill it before the first round
+  uint32_t round0 = 0;            // number of the first round (its parity selects the mask halves)
 };
 
 struct PlainArgs {

@@ -72,7 +72,8 @@ class fg_tune_report(ctypes.Structure):
 class fg_server_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("lanes", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("full_grid", ctypes.c_int32), ("alpha", ctypes.c_float), ("eps", ctypes.c_float),
-                ("hbm_budget", ctypes.c_int64), ("opts", fg_opts * 3)]
+                ("hbm_budget", ctypes.c_int64), ("opts", fg_opts * 3),
+                ("continuous", ctypes.c_int32), ("slots", ctypes.c_int32)]
 
 
 class fg_request_info(ctypes.Structure):
