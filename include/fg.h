@@ -121,6 +121,12 @@ typedef struct {
                                (SSSP) bounds each round to values below the group's smallest
                                pending value plus the window; delta, bucket, yield_edges,
                                emit_capacity and threads_per_vertex do not apply */
+    int32_t group_order;    /* group engine: 0 (default) = the batch's queries are ordered by the
+                               number of arcs within two hops of their source, largest first,
+                               before they are cut into groups, so that a group's queries reach
+                               the same vertices in the same rounds and share more of each
+                               partition visit (results still go to the caller's rows);
+                               1 = groups follow the order of src */
 } fg_opts;
 
 /* counters of the last completed batch on a graph (read by fg_stats after fg_sync) */

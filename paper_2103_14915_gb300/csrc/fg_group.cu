@@ -616,12 +616,13 @@ done:
   }
 }
 
-// D[group][v][g] (internal order) -> out[group * G + g][orig(v)] for v < n.
-// A block moves 32 vertices of one group: 32 * G words read as whole lines,
-// transposed in shared memory, written as G runs of 32 values.
+// D[group][v][g] (internal order) -> out[row(group * G + g)][orig(v)] for v < n,
+// row(j) = rowmap[j] (or j without a map). A block moves 32 vertices of one
+// group: 32 * G words read as whole lines, transposed in shared memory,
+// written as G runs of 32 values.
 __global__ void __launch_bounds__(256) group_out_kernel(const uint32_t *D, uint32_t *out, const int32_t *orig,
-                                                        int64_t n, int64_t npad, int32_t G, int32_t glog2,
-                                                        int32_t nq, int64_t tiles_per_group) {
+                                                        const int32_t *rowmap, int64_t n, int64_t npad, int32_t G,
+                                                        int32_t glog2, int32_t nq, int64_t tiles_per_group) {
   __shared__ uint32_t t[32][33];
   const int64_t grp = blockIdx.x / tiles_per_group;
   const int64_t v0 = (blockIdx.x % tiles_per_group) * 32;
@@ -636,8 +637,57 @@ __global__ void __launch_bounds__(256) group_out_kernel(const uint32_t *D, uint3
     const int64_t q = grp * G + gq, v = v0 + vl;
     if (q < nq && v < n) {
       const int64_t o = orig ? (int64_t)orig[v] : v;
-      out[q * n + o] = t[gq][vl];
+      const int64_t r = rowmap ? (int64_t)rowmap[q] : q;
+      out[r * n + o] = t[gq][vl];
     }
+  }
+}
+
+// Two-hop reach of each query's source: the sum of its out-neighbours' degrees
+// (one warp per query; an out-of-range source gets 0 and is reported by the
+// engine's INIT).
+__global__ void __launch_bounds__(256) group_key_kernel(DevGraph G, const int32_t *src, int32_t nq,
+                                                        unsigned long long *key) {
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (q >= nq) return;
+  const int32_t s = src[q];
+  unsigned long long sum = 0;
+  if (s >= 0 && s < G.n) {
+    const uint32_t v = G.intl ? (uint32_t)G.intl[s] : (uint32_t)s;
+    const uint32_t e0 = G.rp[v], e1 = G.rp[v + 1];
+    for (uint32_t e = e0 + (uint32_t)lane; e < e1; e += 32u) {
+      const uint32_t u = G.adj[e];
+      sum += (unsigned long long)(G.rp[u + 1] - G.rp[u]);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
+  if (lane == 0) key[q] = sum;
+}
+
+// Slot of each query: the number of queries with a larger key, or the same key
+// and a smaller index (a stable descending order). Keys are read in tiles of
+// 1,024 through shared memory.
+__global__ void __launch_bounds__(256) group_rank_kernel(const unsigned long long *key, const int32_t *src,
+                                                         int32_t nq, int32_t *perm, int32_t *psrc) {
+  __shared__ unsigned long long tk[1024];
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long kq = q < nq ? key[q] : 0ull;
+  int64_t rank = 0;
+  for (int64_t t0 = 0; t0 < nq; t0 += 1024) {
+    const int64_t cnt = nq - t0 < 1024 ? nq - t0 : 1024;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) tk[i] = key[t0 + i];
+    __syncthreads();
+    if (q < nq)
+      for (int64_t i = 0; i < cnt; ++i) {
+        const unsigned long long k = tk[i];
+        rank += (k > kq || (k == kq && t0 + i < q)) ? 1 : 0;
+      }
+  }
+  if (q < nq) {
+    perm[rank] = (int32_t)q;
+    psrc[rank] = src[q];
   }
 }
 
@@ -650,6 +700,13 @@ static const void *group_fn(int qtype, int G) {
   if (G == 8) return (const void *)group_kernel<Q_SSSP, 8>;
   if (G == 16) return (const void *)group_kernel<Q_SSSP, 16>;
   return (const void *)group_kernel<Q_SSSP, 32>;
+}
+
+bool group_fits(int S, int G) {
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+  return group_smem_bytes(S, G) <= (size_t)optin;
 }
 
 cudaError_t group_grid_size(int S, int G, int *blocks, int *threads, size_t *smem) {
@@ -679,12 +736,23 @@ cudaError_t launch_group(const GroupArgs &a, int blocks, int threads, size_t sme
   return cudaLaunchCooperativeKernel(group_fn(a.qtype, a.G), dim3(blocks), dim3(threads), args, smem, s);
 }
 
-cudaError_t launch_group_out(const GroupArgs &a, uint32_t *out, cudaStream_t s) {
+cudaError_t launch_group_out(const GroupArgs &a, uint32_t *out, const int32_t *rowmap, cudaStream_t s) {
   const int64_t n = a.g.n;
   const int64_t tiles = (n + 31) / 32;
   const int64_t grid = tiles * (int64_t)a.ngroups;
   if (grid <= 0) return cudaSuccess;
-  group_out_kernel<<<(unsigned)grid, 256, 0, s>>>(a.D, out, a.g.orig, n, a.npad, a.G, a.glog2, a.nq, tiles);
+  group_out_kernel<<<(unsigned)grid, 256, 0, s>>>(a.D, out, a.g.orig, rowmap, n, a.npad, a.G, a.glog2, a.nq, tiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_order(const DevGraph &g, const int32_t *src, int32_t nq, unsigned long long *key,
+                               int32_t *perm, int32_t *psrc, cudaStream_t s) {
+  if (nq <= 0) return cudaSuccess;
+  const int64_t warps_grid = ((int64_t)nq * 32 + 255) / 256;
+  group_key_kernel<<<(unsigned)warps_grid, 256, 0, s>>>(g, src, nq, key);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  group_rank_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(key, src, nq, perm, psrc);
   return cudaGetLastError();
 }
 

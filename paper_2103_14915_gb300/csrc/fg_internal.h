@@ -170,10 +170,20 @@ cudaError_t launch_ppr_finalize(const EngineArgs &a, double *mass, float *p_out,
 cudaError_t launch_permute_out(const uint32_t *state, uint32_t *out, const int32_t *orig, int64_t n, int64_t rows,
                                cudaStream_t s);
 cudaError_t plain_grid_size(int *blocks, int *threads);
+// Whether a group-engine block for partitions of S vertices and groups of G
+// fits the device's shared memory per block.
+bool group_fits(int S, int G);
 cudaError_t group_grid_size(int S, int G, int *blocks, int *threads, size_t *smem);
 cudaError_t launch_group(const GroupArgs &a, int blocks, int threads, size_t smem, cudaStream_t s);
+// Orders a batch's queries for the group engine: key[q] = arcs within two hops
+// of src[q]; perm[j] = the query in slot j (keys descending, ties by index),
+// psrc[j] = src[perm[j]]. key, perm and psrc hold nq entries each.
+cudaError_t launch_group_order(const DevGraph &g, const int32_t *src, int32_t nq, unsigned long long *key,
+                               int32_t *perm, int32_t *psrc, cudaStream_t s);
 // group-engine state (internal order, vertex-major in groups) -> caller's query-major rows
-cudaError_t launch_group_out(const GroupArgs &a, uint32_t *out, cudaStream_t s);
+// Writes the launch's rows to out: slot j's row to out[rowmap[j] * n], or to
+// out[j * n] when rowmap is null.
+cudaError_t launch_group_out(const GroupArgs &a, uint32_t *out, const int32_t *rowmap, cudaStream_t s);
 cudaError_t launch_plain(const PlainArgs &a, int blocks, int threads, cudaStream_t s);
 
 // runtime services for entry points outside fg_runtime.cpp

@@ -470,6 +470,7 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
     return fail(FG_ERR_INVALID_ARG, "threads_per_vertex must be 0, 1 or 32");
   if (o.group != 0 && o.group != 1 && o.group != 8 && o.group != 16 && o.group != 32)
     return fail(FG_ERR_INVALID_ARG, "group must be 0, 1, 8, 16 or 32");
+  if (o.group_order != 0 && o.group_order != 1) return fail(FG_ERR_INVALID_ARG, "group_order must be 0 or 1");
   if (qtype == Q_PPR) o.sched = FG_SCHED_FIFO;  // PPR buffers are scheduled first-in first-out
   const uint32_t max_rounds = o.max_rounds ? o.max_rounds : 1000000u;
   const uint64_t watchdog_ns = (uint64_t)(o.watchdog_ms ? o.watchdog_ms : 30000u) * 1000000ull;
@@ -571,6 +572,8 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
       nbq = std::min<int64_t>(nbq, nq);
     }
     const int gi = glog2 - 3;
+    if (!group_fits(g->S, Gq))
+      return fail(FG_ERR_UNSUPPORTED, "group %d does not fit shared memory with partitions of %d vertices", Gq, g->S);
     if (g->group_blocks[gi] == 0)
       CUDA_TRY(group_grid_size(g->S, Gq, &g->group_blocks[gi], &g->group_threads[gi], &g->group_smem[gi]));
     const int blocks = grid_div > 1 ? std::max(1, g->group_blocks[gi] / grid_div) : g->group_blocks[gi];
@@ -586,6 +589,21 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
     CUDA_TRY(ws.ctrl.reserve(sizeof(Ctrl)));
     d_ctrl = ws.ctrl.as<Ctrl>();
     CUDA_TRY(cudaMemsetAsync(d_ctrl, 0, sizeof(Ctrl), stream));
+    // queries ordered by two-hop reach, so each group's (and each launch's)
+    // queries advance through the graph in step; rows go back to the caller's order
+    const bool reorder = o.group_order == 0 && nq > Gq;
+    const int32_t *gsrc = src;
+    const int32_t *rowmap = nullptr;
+    if (reorder) {
+      CUDA_TRY(ws.g_key.reserve(8 * (size_t)nq));
+      CUDA_TRY(ws.g_perm.reserve(4 * (size_t)nq));
+      CUDA_TRY(ws.g_psrc.reserve(4 * (size_t)nq));
+      CUDA_TRY(launch_group_order(g->dg, src, (int32_t)nq, ws.g_key.as<unsigned long long>(), ws.g_perm.as<int32_t>(),
+                                  ws.g_psrc.as<int32_t>(), stream));
+      launches += 2;
+      gsrc = ws.g_psrc.as<int32_t>();
+      rowmap = ws.g_perm.as<int32_t>();
+    }
     for (int64_t q0 = 0; q0 < nq; q0 += nbq) {
       const int64_t cnt_q = std::min<int64_t>(nbq, nq - q0);
       GroupArgs a;
@@ -596,7 +614,7 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
       a.glog2 = glog2;
       a.ngroups = (int32_t)((cnt_q + Gq - 1) / Gq);
       a.npad = npad;
-      a.src = src + q0;
+      a.src = gsrc + q0;
       a.D = ws.g_D.as<uint32_t>();
       a.pend = ws.g_pend.as<uint32_t>();
       a.dirty = ws.g_dirty.as<uint32_t>();
@@ -612,7 +630,8 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
       a.watchdog_ns = watchdog_ns;
       CUDA_TRY(launch_group(a, blocks, g->group_threads[gi], g->group_smem[gi], stream));
       ++launches;
-      CUDA_TRY(launch_group_out(a, dist + (size_t)q0 * (size_t)n, stream));
+      if (rowmap) CUDA_TRY(launch_group_out(a, dist, rowmap + q0, stream));
+      else CUDA_TRY(launch_group_out(a, dist + (size_t)q0 * (size_t)n, nullptr, stream));
       ++launches;
     }
   } else if (o.mode == FG_MODE_BUFFERED) {

@@ -189,6 +189,8 @@ fg_status create_slot_lane(fg_server *s, SlotLane &C, int kind, int nslots, int 
   C.gi = C.glog2 - 3;
   C.ngroups = nslots / G;
   C.nslots = nslots;
+  if (!group_fits(g->S, G))
+    return fail(FG_ERR_UNSUPPORTED, "group %d does not fit shared memory with partitions of %d vertices", G, g->S);
   if (g->group_blocks[C.gi] == 0)
     CUDA_TRY(group_grid_size(g->S, G, &g->group_blocks[C.gi], &g->group_threads[C.gi], &g->group_smem[C.gi]));
   C.blocks = div > 1 ? std::max(1, g->group_blocks[C.gi] / div) : g->group_blocks[C.gi];

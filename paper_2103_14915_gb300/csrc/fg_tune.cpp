@@ -123,7 +123,7 @@ extern "C" fg_status fg_tune_opts_ex(fg_graph *g, int32_t kind, const int32_t *s
   const int auto_group = (g->m > 0 && 2 * g->cut > g->m) ? 16 : 1;
   if (kind != FG_QUERY_PPR) {
     for (int G : {1, 16, 32}) {
-      if (G == auto_group) continue;
+      if (G == auto_group || (G > 1 && !group_fits(g->S, G))) continue;
       fg_opts o = base;
       o.group = G;
       if ((st = try_opts(o)) != FG_OK) return st;

@@ -135,11 +135,14 @@ def test_group_engine_split_batches_and_stats():
     try:
         srcs = inputs.sources_uniform(g, 50, 2)
         ref = oracle.sssp(g, srcs)
-        got = run(h, g, "sssp", srcs, group=8, query_batch=16)  # four launches, the last one partial
+        got = run(h, g, "sssp", srcs, group=8, query_batch=16, group_order=1)  # four launches, the last partial
         assert np.array_equal(got, ref)
         st, s = fg.fg_stats(h)
         fg.check(st)
         assert s.launches == 8 and s.rounds > 0 and s.visits > 0
+        got = run(h, g, "sssp", srcs, group=8, query_batch=16)  # the same after ordering (two more kernels)
+        assert np.array_equal(got, ref)
+        assert fg.fg_stats(h)[1].launches == 10
         # lane relaxations cover at least the arcs a sequential Dijkstra scans
         deg = np.diff(g.row_ptr)
         dijkstra_arcs = int(sum(deg[ref[q] != 0xFFFFFFFF].sum() for q in range(len(srcs))))
@@ -170,5 +173,38 @@ def test_group_option_is_checked_on_the_host():
         s_d = torch.zeros(1, dtype=torch.int32, device=DEV)
         out = torch.empty((1, g.n), dtype=torch.int32, device=DEV)
         assert fg.fg_sssp_batch(h, s_d, 1, out, None, fg.fg_default_opts(group=12)) == fg.FG_ERR_INVALID_ARG
+    finally:
+        fg.fg_graph_destroy(h)
+
+
+@pytest.mark.parametrize("G", [8, 32])
+def test_group_order_keeps_rows(G):
+    """Queries are regrouped by two-hop reach inside the library; every row still
+    belongs to its own source, with duplicates, hubs, isolated vertices and
+    launches split by query_batch, for both group orders."""
+    g = inputs.rmat(11, 16, seed=13, weights=(1, 255))
+    h = create(g, fg.FG_PART_RANGE, 64)
+    try:
+        deg = np.diff(g.row_ptr)
+        srcs = inputs.sources_uniform(g, 3 * G + 5, 21).astype(np.int32)
+        srcs[4] = srcs[9]                     # duplicate
+        srcs[5] = int(np.argmax(deg))         # the largest hub
+        if (deg == 0).any():
+            srcs[6] = int(np.flatnonzero(deg == 0)[0])  # no arcs
+        for kind in ("sssp", "bfs"):
+            ref = oracle.sssp(g, srcs) if kind == "sssp" else oracle.bfs(g, srcs)
+            for order in (0, 1):
+                for qb in (0, G + 3):
+                    got = run(h, g, kind, srcs, group=G, group_order=order, query_batch=qb)
+                    assert np.array_equal(got, ref), (kind, order, qb)
+        # an out-of-range source among reordered queries is still reported
+        bad = srcs.copy()
+        bad[7] = g.n
+        s_d = torch.from_numpy(bad).to(DEV)
+        out = torch.empty((len(bad), g.n), dtype=torch.int32, device=DEV)
+        fg.check(fg.fg_sssp_batch(h, s_d, len(bad), out, None, fg.fg_default_opts(group=G)))
+        assert fg.fg_sync() == fg.FG_ERR_INVALID_ARG
+        assert fg.fg_sssp_batch(h, s_d, len(bad), out, None, fg.fg_default_opts(group=G, group_order=2)) \
+            == fg.FG_ERR_INVALID_ARG
     finally:
         fg.fg_graph_destroy(h)
