@@ -93,12 +93,12 @@ constexpr uint32_t kNoArc = 0xFFFFFFFFu;
 template <int QT, int GQ>
 __device__ __forceinline__ void g_step(const GroupArgs &a, const uint4 *sarc, const uint32_t *sdv_g,
                                        uint32_t dv_own, uint32_t *Dg_g, uint32_t *pend_g, uint32_t *dirty_g,
-                                       uint32_t *gbest_n, int g, int h, uint32_t &relaxed, uint32_t &improved,
-                                       uint32_t &lanes_marked) {
+                                       uint32_t *gbest_n, int g, int h, uint32_t &improved,
+                                       uint32_t &lanes_marked, bool chk) {
   constexpr int LG = ilog2c(GQ), SL = 32 / GQ;
   constexpr unsigned GM = GQ == 32 ? 0xFFFFFFFFu : ((1u << GQ) - 1u);
   const int slog2 = a.g.slog2;
-#pragma unroll
+#pragma unroll 1
   for (int j0 = 0; j0 < 32; j0 += SL * kGUnroll) {
     uint32_t nd[kGUnroll], cur[kGUnroll];
     bool act[kGUnroll];
@@ -109,7 +109,7 @@ __device__ __forceinline__ void g_step(const GroupArgs &a, const uint4 *sarc, co
       if (e.z != kNoArc) dv = sdv_g != nullptr ? sdv_g[e.z << LG] : dv_own;
       act[q] = dv != kInf;
       uint32_t sum = dv + (QT == Q_BFS ? 1u : e.y);
-      if (act[q] && (sum < dv || sum == kInf)) {  // 2^32 - 1 reached: saturate and report
+      if (QT != Q_BFS && chk && act[q] && (sum < dv || sum == kInf)) {  // 2^32 - 1 reached: saturate and report
         atomicCAS(&a.ctrl->status, 0, (int)FG_ERR_OVERFLOW);
         sum = kInf - 1u;
       }
@@ -119,7 +119,6 @@ __device__ __forceinline__ void g_step(const GroupArgs &a, const uint4 *sarc, co
 #pragma unroll
     for (int q = 0; q < kGUnroll; ++q) {
       const bool imp = act[q] && nd[q] < cur[q];
-      relaxed += act[q] ? 1u : 0u;
       const uint32_t uq = sarc[j0 + q * SL + h].x;  // read again rather than held in a register
       if (imp) atomicMin(Dg_g + ((size_t)uq << LG), nd[q]);
       const unsigned im = __ballot_sync(kFull, imp);
@@ -195,6 +194,8 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
   const uint64_t K = (uint64_t)a.ngroups * (uint64_t)G.nparts;
   const uint64_t tid = (uint64_t)blockIdx.x * kGThreads + threadIdx.x, nthr = (uint64_t)gridDim.x * kGThreads;
   const size_t row = (size_t)a.npad;  // vertices per group row
+  // values at or above ovf_lim can overflow when a weight is added
+  const uint32_t ovf_lim = G.max_w >= kInf - 1u ? 0u : kInf - 1u - G.max_w;
 
   // ---- K0: state and masks (InitBuffers, first half); in serve mode only on
   //      the first launch on the state (later launches resume it) ----
@@ -477,7 +478,7 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
         // it asks L2 for the arc's target line (prefetch.global.L2), so the
         // relaxation's loads of target values find their lines on chip
         // without holding registers while they travel.
-        auto run = [&](uint32_t nsteps, auto make, const uint32_t *sdv_g, uint32_t dv_own) {
+        auto run = [&](uint32_t nsteps, auto make, const uint32_t *sdv_g, uint32_t dv_own, bool chk) {
           const uint4 none = make_uint4(0u, 1u, kNoArc, 0u);
           uint4 a0 = make(0u);
           uint4 a1 = nsteps > 1u ? make(1u) : none;
@@ -487,7 +488,7 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
             __syncwarp();
             if (a1.z != kNoArc) prefetch_l2(Dg + ((size_t)a1.x << LG));
             const uint4 a2 = i + 2u < nsteps ? make(i + 2u) : none;
-            g_step<QT, GQ>(a, sarc, sdv_g, dv_own, Dg_g, pend_g, dirty_g, gb_n, g, h, r32, i32, gacc);
+            g_step<QT, GQ>(a, sarc, sdv_g, dv_own, Dg_g, pend_g, dirty_g, gb_n, g, h, i32, gacc, chk);
             __syncwarp();  // sarc is rewritten by the next step
             a0 = a1;
             a1 = a2;
@@ -496,12 +497,18 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
         if (d.kind == kItemHub) {
           uint32_t dv = kInf;
           if (((d.m >> g) & 1u) != 0u) dv = __ldcg(Dg_g + ((size_t)d.pv << LG));
+          // a sum can reach 2^32 - 1 only from a value within max_w of it
+          const bool chk_hub = __any_sync(kFull, dv != kInf && dv >= ovf_lim);
           for (;;) {
             uint32_t s0 = 0;
             if (lane == 0) s0 = atomicAdd(&s_desc[k].next, 4u);  // four steps of 32 arcs at a time
             s0 = __shfl_sync(kFull, s0, 0);
             if (s0 >= d.n) break;
             const uint32_t ns = d.n - s0 < 4u ? d.n - s0 : 4u;
+            if (dv != kInf) {  // this lane relaxes every arc of the claimed steps
+              const uint32_t e_lo = d.eb + s0 * 32u, e_hi = d.eb + (s0 + ns) * 32u;
+              r32 += (e_hi < d.ee ? e_hi : d.ee) - e_lo;
+            }
             auto make = [&](uint32_t i) {
               const uint32_t e = d.eb + (s0 + i) * 32u + (uint32_t)lane;
               const bool has = e < d.ee;
@@ -510,7 +517,7 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
                                 (has && QT != Q_BFS && G.wt != nullptr) ? __ldg(G.wt + e) : 1u,
                                 has ? 0u : kNoArc, 0u);
             };
-            run(ns, make, nullptr, dv);
+            run(ns, make, nullptr, dv, chk_hub);
           }
         } else {
           const uint32_t base = d.pv << G.slog2;
@@ -538,6 +545,7 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
             // L of sdv holds vertex L's values of the group, kInf where not
             // pending. Under a window, values at or beyond the group's bound
             // stay pending for a later round (Delta-stepping across rounds).
+            bool big = false;  // some source value within max_w of 2^32 - 1 (sums need the check)
 #pragma unroll 4
             for (int L0 = 0; L0 < 32; L0 += SL) {
               const int L = L0 + h;
@@ -561,6 +569,9 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
                 if (def) dd = kInf;
               }
               sdv[(L << LG) + g] = dd;
+              big |= dd != kInf && dd >= ovf_lim;
+              const uint32_t degL = __shfl_sync(kFull, deg, L);
+              if (dd != kInf) r32 += degL;  // this lane relaxes every arc of vertex L
             }
             __syncwarp();
             auto make = [&](uint32_t i) {
@@ -573,7 +584,7 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
                                 (has && QT != Q_BFS && G.wt != nullptr) ? __ldg(G.wt + eL) : 1u,
                                 has ? (uint32_t)L : kNoArc, 0u);
             };
-            run((tot + 31u) / 32u, make, sdv + g, kInf);
+            run((tot + 31u) / 32u, make, sdv + g, kInf, __any_sync(kFull, big));
             __syncwarp();  // sdv is rewritten by the next batch
           }
         }

@@ -142,6 +142,7 @@ struct fg_graph {
   int engine_qtype = -1;
   uint32_t max_degree = 0;
   double mean_weight = 1.0;        // mean arc weight (1 when unweighted)
+  uint32_t max_weight = 0;         // largest arc weight (0 when unweighted)
   // choices of fg_tune_opts[_ex], keyed by (query kind, log2 of the batch size
   // rounded up, and for PPR the bits of alpha and eps)
   std::map<fg::TuneKey, std::pair<fg_opts, fg_tune_report>> tuned;

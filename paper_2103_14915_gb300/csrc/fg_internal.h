@@ -27,6 +27,7 @@ struct DevGraph {
   int32_t nparts = 0;
   uint64_t m = 0;
   uint32_t max_deg = 0;            // largest out-degree (bounds every arc loop)
+  uint32_t max_w = 1;              // largest arc weight (1 when unweighted)
   const uint32_t *rp = nullptr;    // [n+1] arc offsets
   const uint32_t *adj = nullptr;   // [m] internal target ids
   const uint32_t *wt = nullptr;    // [m] weights, or null (unit)

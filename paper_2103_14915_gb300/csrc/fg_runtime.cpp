@@ -283,6 +283,7 @@ extern "C" fg_status fg_graph_create_ex(int64_t n, int64_t m, const int64_t *row
     for (int64_t e = 0; e < m; ++e) {
       sum += (double)i_wt[(size_t)e];
       if (i_wt[(size_t)e] == 0u) g->has_zero_weight = true;
+      g->max_weight = std::max(g->max_weight, i_wt[(size_t)e]);
     }
     if (m > 0) g->mean_weight = sum / (double)m;
   }
@@ -316,6 +317,7 @@ extern "C" fg_status fg_graph_create_ex(int64_t n, int64_t m, const int64_t *row
   d.nparts = g->nparts;
   d.m = (uint64_t)m;
   d.max_deg = g->max_degree;
+  d.max_w = wt ? g->max_weight : 1u;
   d.rp = g->rp.as<uint32_t>();
   d.adj = g->adj.as<uint32_t>();
   d.wt = wt ? g->wt.as<uint32_t>() : nullptr;
