@@ -127,6 +127,10 @@ typedef struct {
                                the same vertices in the same rounds and share more of each
                                partition visit (results still go to the caller's rows);
                                1 = groups follow the order of src */
+    int32_t check_staging;  /* group engine self-test: 1 = after each shared-memory staging wait,
+                               compare every staged row offset and pending mask with global
+                               memory and report FG_ERR_CUDA (site: staged words differ) on a
+                               mismatch; 0 (default) = off */
 } fg_opts;
 
 /* counters of the last completed batch on a graph (read by fg_stats after fg_sync) */

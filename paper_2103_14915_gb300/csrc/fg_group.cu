@@ -417,6 +417,14 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
             break;
           }
           tma_bits ^= 1u << k;
+          if (a.check_staging) {
+            // self-test: the landed words equal global memory (row offsets
+            // never change; this round's masks change only when cleared below)
+            bool bad = false;
+            for (int i = lane; i < S + 4; i += 32) bad |= rp_s[i] != __ldg(G.rp + base + i);
+            for (int i = lane; i < S; i += 32) bad |= pm_s[i] != __ldcg(pm_g + i);
+            if (__any_sync(kFull, bad) && lane == 0) raise_status(c, FG_ERR_CUDA, kSiteStageCheck);
+          }
           // this round's masks of the item are taken: clear them for reuse
           for (int i = lane; i < (S >> 2); i += 32) reinterpret_cast<uint4 *>(pm_g)[i] = make_uint4(0u, 0u, 0u, 0u);
           // list the pending vertices with an arc, and the prefix of their arcs

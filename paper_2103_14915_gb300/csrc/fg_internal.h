@@ -16,7 +16,7 @@ constexpr uint32_t kInvalidKey = 0xFFFFFFFFu;
 
 // where a device status was raised (reported by fg_sync)
 enum : unsigned { kSiteNone = 0, kSiteBarrier = 1, kSiteStage = 2, kSiteVisit = 3, kSiteRounds = 4,
-                  kSiteSource = 5, kSiteArena = 6, kSiteDegree = 7, kSiteClaim = 8 };
+                  kSiteSource = 5, kSiteArena = 6, kSiteDegree = 7, kSiteClaim = 8, kSiteStageCheck = 9 };
 
 // Graph in partition-major ("internal") vertex order. Partition j holds the
 // internal ids [j*S, (j+1)*S); S = 1 << slog2.
@@ -141,6 +141,7 @@ struct GroupArgs {
   uint32_t *occ = nullptr;        // [ngroups] lanes holding an admitted, unfinished query
   uint32_t *seen = nullptr;       // [slots] sequence number of each slot's current request
   uint32_t *gact = nullptr;       // [2][ngroups] lanes with pending work in the round of that parity
+  uint32_t check_staging = 0;     // 1: compare every staged word with global memory (self-test)
   uint32_t init = 0;              // 1: first launch on this state: fill it before the first round
   uint32_t round0 = 0;            // number of the first round (its parity selects the mask halves)
 };

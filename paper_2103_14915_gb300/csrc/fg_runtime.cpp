@@ -473,6 +473,7 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
   if (o.group != 0 && o.group != 1 && o.group != 8 && o.group != 16 && o.group != 32)
     return fail(FG_ERR_INVALID_ARG, "group must be 0, 1, 8, 16 or 32");
   if (o.group_order != 0 && o.group_order != 1) return fail(FG_ERR_INVALID_ARG, "group_order must be 0 or 1");
+  if (o.check_staging != 0 && o.check_staging != 1) return fail(FG_ERR_INVALID_ARG, "check_staging must be 0 or 1");
   if (qtype == Q_PPR) o.sched = FG_SCHED_FIFO;  // PPR buffers are scheduled first-in first-out
   const uint32_t max_rounds = o.max_rounds ? o.max_rounds : 1000000u;
   const uint64_t watchdog_ns = (uint64_t)(o.watchdog_ms ? o.watchdog_ms : 30000u) * 1000000ull;
@@ -630,6 +631,7 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
       a.ctrl = d_ctrl;
       a.max_rounds = max_rounds;
       a.watchdog_ns = watchdog_ns;
+      a.check_staging = o.check_staging ? 1u : 0u;
       CUDA_TRY(launch_group(a, blocks, g->group_threads[gi], g->group_smem[gi], stream));
       ++launches;
       if (rowmap) CUDA_TRY(launch_group_out(a, dist, rowmap + q0, stream));
@@ -870,9 +872,10 @@ extern "C" fg_status fg_sync(void *stream_v) {
                              "operation buffer overflow", "distance overflow", "unsupported"};
       const char *sites[] = {"", " (device-wide barrier wait)", " (shared-memory staging wait)",
                              " (visit step limit)", " (max_rounds)", " (source id out of range)",
-                             " (operation arena)", " (vertex degree out of range)", " (work-item claim wait)"};
+                             " (operation arena)", " (vertex degree out of range)", " (work-item claim wait)",
+                             " (staged words differ from global memory)"};
       const int k = c.status >= 0 && c.status <= 7 ? c.status : 3;
-      const unsigned si = c.site <= 8 ? c.site : 0;
+      const unsigned si = c.site <= 9 ? c.site : 0;
       first = fail((fg_status)c.status, "device reported: %s%s", names[k], sites[si]);
     }
     std::lock_guard<std::mutex> lp(g_pending_mu);

@@ -46,7 +46,7 @@ class fg_opts(ctypes.Structure):
                 ("yield_edges", ctypes.c_uint64), ("max_rounds", ctypes.c_uint32),
                 ("watchdog_ms", ctypes.c_uint32), ("emit_capacity", ctypes.c_uint64),
                 ("host_io", ctypes.c_int32), ("query_batch", ctypes.c_int32), ("threads_per_vertex", ctypes.c_int32),
-                ("group", ctypes.c_int32), ("group_order", ctypes.c_int32)]
+                ("group", ctypes.c_int32), ("group_order", ctypes.c_int32), ("check_staging", ctypes.c_int32)]
 
 
 class fg_stats_t(ctypes.Structure):
