@@ -110,7 +110,7 @@ typedef struct {
                                with out-degree <= 8 only), 32 or 0 (default) = a warp shares
                                a batch of 32 frontier vertices' arcs evenly */
     int32_t group;          /* SSSP/BFS queries that share one partition visit lane by lane
-                               (the query group): 8, 16 or 32 = the group engine, whose state
+                               (the query group): 8, 16, 32 or 64 = the group engine, whose state
                                keeps a group's values of one vertex in one line, so one access
                                and one read of the arcs serve the whole group (best where almost
                                every arc leaves its partition: power-law graphs); 1 = one query
@@ -119,8 +119,9 @@ typedef struct {
                                than half of the graph's arcs cross partitions, else 1. PPR
                                always runs one query per warp. In the group engine, sched_window
                                (SSSP) bounds each round to values below the group's smallest
-                               pending value plus the window; delta, bucket, yield_edges,
-                               emit_capacity and threads_per_vertex do not apply */
+                               pending value plus the window (groups of 8 to 32 only: a group of
+                               64 with a window is FG_ERR_UNSUPPORTED); delta, bucket,
+                               yield_edges, emit_capacity and threads_per_vertex do not apply */
     int32_t group_order;    /* group engine: 0 (default) = the batch's queries are ordered by the
                                number of arcs within two hops of their source, largest first,
                                before they are cut into groups, so that a group's queries reach

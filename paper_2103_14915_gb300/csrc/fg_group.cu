@@ -38,6 +38,7 @@
 // dirty[(r + 1) & 1]; a (partition, group)'s masks of round r are cleared by
 // its visit, a hub's by the scan, so both halves are zero again when reused.
 #include <cstdio>
+#include <type_traits>
 
 #include "fg_device.cuh"
 
@@ -55,16 +56,43 @@ struct ItemDesc {
   uint32_t grp;   // group
   uint32_t pv;    // partition (kItemPart) or hub vertex (kItemHub)
   uint32_t n;     // listed vertices (kItemPart) or steps of 32 arcs (kItemHub)
-  uint32_t eb, ee, m;  // hub chunk: arc range and the lanes pending on the hub
+  uint32_t eb, ee;  // hub chunk: arc range
   uint32_t next;  // claim counter of the consumers (vertices or steps)
+  uint32_t pad;
+  unsigned long long m;  // hub chunk: the lanes pending on the hub
 };
 
-// Shared memory: two item buffers (row offsets, pending masks, listed
-// vertices, their arc prefix), then per consumer warp the current step's 32
-// arcs (uint4 each) and one [32][G] table of source values.
-__host__ __device__ inline size_t group_item_words(int S) { return (size_t)(S + 4) * 2 + (size_t)S * 2; }
+// Lane layout by group size. G <= 32: lane (h, g) holds query g of the group
+// for arc slot h (SL = 32 / G arcs per warp step), and a vertex's pending
+// lanes are a 32-bit mask. G = 64: lane l holds queries 2l and 2l + 1 (one
+// 8-byte pair of the vertex's line), one arc per warp step, and the mask is 64
+// bits with query 2l + j at bit 32j + l, so that a warp ballot per half is a
+// mask word.
+template <int GQ>
+struct GroupLanes {
+  using M = uint32_t;
+  static constexpr int SL = 32 / GQ;
+};
+template <>
+struct GroupLanes<64> {
+  using M = unsigned long long;
+  static constexpr int SL = 1;
+};
+template <int GQ>
+__host__ __device__ __forceinline__ typename GroupLanes<GQ>::M group_bit(uint32_t gq) {
+  if constexpr (GQ == 64) return 1ull << (((gq & 1u) << 5) | (gq >> 1));
+  else return 1u << gq;
+}
+
+// Shared memory: two item buffers (row offsets, pending masks of one or two
+// words, listed vertices), then per consumer warp the current step's 32 arcs
+// (uint4 each) and one [32][G] table of source values.
+__host__ __device__ inline size_t group_mask_words(int G) { return G == 64 ? 2u : 1u; }
+__host__ __device__ inline size_t group_item_words(int S, int G) {
+  return (size_t)(S + 4) + (size_t)S * (1u + group_mask_words(G));
+}
 __host__ __device__ inline size_t group_smem_bytes(int S, int G) {
-  return (2 * group_item_words(S) + (size_t)kGCons * (128u + 32u * (size_t)G)) * sizeof(uint32_t);
+  return (2 * group_item_words(S, G) + (size_t)kGCons * (128u + 32u * (size_t)G)) * sizeof(uint32_t);
 }
 
 __device__ __forceinline__ uint32_t g_relax(Ctrl *c, uint32_t d, uint32_t w) {
@@ -140,8 +168,61 @@ __device__ __forceinline__ void g_step(const GroupArgs &a, const uint4 *sarc, co
   }
 }
 
+// The same step for groups of 64: lane l compares and lowers the pair of
+// values of queries 2l and 2l + 1 (one 8-byte load of the target's line per
+// arc for the warp's 256 bytes), and lane 0 marks the improved lanes of both
+// halves in the 64-bit mask. sdv2 = the warp's [32][32] table of value pairs
+// + l, or null with dv_own (a hub chunk); Dg_p = the group's state + 2l.
+template <int QT>
+__device__ __forceinline__ void g_step64(const GroupArgs &a, const uint4 *sarc, const uint2 *sdv2, uint2 dv_own,
+                                         uint32_t *Dg_p, unsigned long long *pend_g, uint32_t *dirty_g, int lane,
+                                         uint32_t &improved, bool chk) {
+  const int slog2 = a.g.slog2;
+#pragma unroll 1
+  for (int j0 = 0; j0 < 32; j0 += kGUnroll) {
+    uint2 nd[kGUnroll], cur[kGUnroll];
+    bool act0[kGUnroll], act1[kGUnroll];
+#pragma unroll
+    for (int q = 0; q < kGUnroll; ++q) {
+      const uint4 e = sarc[j0 + q];  // one broadcast read
+      uint2 dv = make_uint2(kInf, kInf);
+      if (e.z != kNoArc) dv = sdv2 != nullptr ? sdv2[e.z << 5] : dv_own;
+      act0[q] = dv.x != kInf;
+      act1[q] = dv.y != kInf;
+      const uint32_t w = QT == Q_BFS ? 1u : e.y;
+      uint32_t s0 = dv.x + w, s1 = dv.y + w;
+      if (QT != Q_BFS && chk) {  // 2^32 - 1 reached: saturate and report
+        if (act0[q] && (s0 < dv.x || s0 == kInf)) {
+          atomicCAS(&a.ctrl->status, 0, (int)FG_ERR_OVERFLOW);
+          s0 = kInf - 1u;
+        }
+        if (act1[q] && (s1 < dv.y || s1 == kInf)) {
+          atomicCAS(&a.ctrl->status, 0, (int)FG_ERR_OVERFLOW);
+          s1 = kInf - 1u;
+        }
+      }
+      nd[q] = make_uint2(s0, s1);
+      cur[q] = (act0[q] || act1[q]) ? *reinterpret_cast<const uint2 *>(Dg_p + ((size_t)e.x << 6)) : make_uint2(0u, 0u);
+    }
+#pragma unroll
+    for (int q = 0; q < kGUnroll; ++q) {
+      const bool i0 = act0[q] && nd[q].x < cur[q].x, i1 = act1[q] && nd[q].y < cur[q].y;
+      const uint32_t uq = sarc[j0 + q].x;  // read again rather than held in a register
+      uint32_t *t = Dg_p + ((size_t)uq << 6);
+      if (i0) atomicMin(t, nd[q].x);
+      if (i1) atomicMin(t + 1, nd[q].y);
+      const unsigned b0 = __ballot_sync(kFull, i0), b1 = __ballot_sync(kFull, i1);
+      if ((b0 | b1) != 0u && lane == 0) {  // most steps improve nothing
+        atomicOr(pend_g + uq, (unsigned long long)b0 | ((unsigned long long)b1 << 32));
+        dirty_g[uq >> slog2] = 1u;
+        improved += (uint32_t)(__popc(b0) + __popc(b1));
+      }
+    }
+  }
+}
+
 template <int QT, int GQ>
-__global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
+__global__ void __launch_bounds__(kGThreads, GQ == 64 ? 2 : 3) group_kernel(GroupArgs a) {
   extern __shared__ __align__(16) uint32_t g_smem[];
   __shared__ __align__(8) uint64_t s_full[2], s_empty[2], s_tma[2];
   __shared__ ItemDesc s_desc[2];
@@ -151,15 +232,17 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
   const int S = G.S;
   constexpr int Gq = GQ;
   constexpr int LG = ilog2c(GQ);
-  constexpr int SL = 32 / GQ;       // arc slots per warp
-  const int g = lane & (Gq - 1);    // query of the group held by this lane
-  const int h = lane >> LG;         // arc slot of this lane
-  const size_t iw = group_item_words(S);
-  // item buffer k: rp [S + 4], pm [S], vid [S], pre [S + 4]
+  using M = typename GroupLanes<GQ>::M;  // pending-mask word of a vertex
+  constexpr int SL = GroupLanes<GQ>::SL;  // arc slots per warp
+  constexpr int MW = (int)sizeof(M) / 4;  // words per mask
+  const int g = lane & (Gq - 1);    // query of the group held by this lane (G = 64: the pair)
+  const int h = GQ == 64 ? 0 : lane >> LG;  // arc slot of this lane
+  const size_t iw = group_item_words(S, Gq);
+  M *const pend = reinterpret_cast<M *>(a.pend);
+  // item buffer k: rp [S + 4], pm [S masks], vid [S]
   auto buf_rp = [&](uint32_t k) { return g_smem + k * iw; };
-  auto buf_pm = [&](uint32_t k) { return g_smem + k * iw + (S + 4); };
-  auto buf_vid = [&](uint32_t k) { return g_smem + k * iw + (S + 4) + S; };
-  auto buf_pre = [&](uint32_t k) { return g_smem + k * iw + (S + 4) + 2 * S; };
+  auto buf_pm = [&](uint32_t k) { return reinterpret_cast<M *>(g_smem + k * iw + (S + 4)); };
+  auto buf_vid = [&](uint32_t k) { return g_smem + k * iw + (S + 4) + MW * S; };
   // per consumer warp: the step's arcs (uint4[32]) and the batch's source values ([32][G])
   uint4 *sarc = reinterpret_cast<uint4 *>(g_smem + 2 * iw) + (size_t)(producer ? 0 : wid) * 32u;
   uint32_t *sdv = g_smem + 2 * iw + (size_t)kGCons * 128u + (size_t)(producer ? 0 : wid) * 32u * (uint32_t)Gq;
@@ -203,7 +286,7 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
     const uint64_t dwords = (uint64_t)a.ngroups * (uint64_t)a.npad * (uint64_t)Gq;
     for (uint64_t i = tid; i < dwords / 4u; i += nthr)
       reinterpret_cast<uint4 *>(a.D)[i] = make_uint4(kInf, kInf, kInf, kInf);
-    const uint64_t pwords = 2ull * (uint64_t)a.ngroups * (uint64_t)a.npad;
+    const uint64_t pwords = 2ull * (uint64_t)a.ngroups * (uint64_t)a.npad * (uint64_t)MW;
     for (uint64_t i = tid; i < pwords / 4u; i += nthr) reinterpret_cast<uint4 *>(a.pend)[i] = make_uint4(0u, 0u, 0u, 0u);
     for (uint64_t i = tid; i < 2ull * K; i += nthr) a.dirty[i] = 0u;
     if (a.gbest)
@@ -225,7 +308,7 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
     const uint32_t v = G.intl ? (uint32_t)G.intl[s] : (uint32_t)s;
     const uint32_t grp = (uint32_t)(q >> a.glog2), gq = (uint32_t)(q & (uint64_t)(Gq - 1));
     a.D[((size_t)grp * row + v) * (size_t)Gq + gq] = 0u;
-    atomicOr(a.pend + (size_t)grp * row + v, 1u << gq);
+    atomicOr(pend + (size_t)grp * row + v, group_bit<GQ>(gq));
     a.dirty[(size_t)grp * G.nparts + (v >> G.slog2)] = 1u;
     if (a.gbest) atomicMin(a.gbest + grp, 0u);
   }
@@ -234,8 +317,8 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
 
   for (uint32_t round = a.round0;; ++round) {
     const uint32_t cur = round & 1u, nxt = cur ^ 1u;
-    uint32_t *pend_c = a.pend + (size_t)cur * (size_t)a.ngroups * row;
-    uint32_t *pend_n = a.pend + (size_t)nxt * (size_t)a.ngroups * row;
+    M *pend_c = pend + (size_t)cur * (size_t)a.ngroups * row;
+    M *pend_n = pend + (size_t)nxt * (size_t)a.ngroups * row;
     uint32_t *dirty_c = a.dirty + (size_t)cur * K;
     uint32_t *dirty_n = a.dirty + (size_t)nxt * K;
     // ---- SCAN: hub chunks, then dirty (partition, group) items ----
@@ -253,15 +336,17 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
       for (uint64_t k = tid; k < HK; k += nthr) {
         const uint32_t grp = (uint32_t)(k / (uint64_t)a.nhubs), hi = (uint32_t)(k % (uint64_t)a.nhubs);
         const uint32_t v = a.hubs[hi];
-        uint32_t *pw = pend_c + (size_t)grp * row + v;
-        const uint32_t m = __ldcg(pw);
+        M *pw = pend_c + (size_t)grp * row + v;
+        const M m = __ldcg(pw);
         if (m == 0u) continue;
         *pw = 0u;
         const uint32_t e0 = G.rp[v], e1 = G.rp[v + 1];
         const uint32_t nch = (e1 - e0 + a.hub_chunk - 1u) / a.hub_chunk;
         const uint32_t b = atomicAdd(&c->g_hub_items[cur], nch);
-        for (uint32_t ch = 0; ch < nch && b + ch < a.hub_cap; ++ch)
-          a.items[b + ch] = make_uint4(grp, v, e0 + ch * a.hub_chunk, m);
+        for (uint32_t ch = 0; ch < nch && b + ch < a.hub_cap; ++ch) {
+          a.items[b + ch] = make_uint4(grp, v, e0 + ch * a.hub_chunk, (uint32_t)m);
+          if constexpr (GQ == 64) a.hub_hi[b + ch] = (uint32_t)(m >> 32);
+        }
         if (b + nch > a.hub_cap) raise_status(c, FG_ERR_BIN_OVERFLOW, kSiteArena);
       }
       const uint64_t gw = tid >> 5, nw = nthr >> 5;
@@ -284,7 +369,9 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
     FG_GPHASE(2);
     const uint32_t n_hub = umin64(*reinterpret_cast<volatile unsigned *>(&c->g_hub_items[cur]), a.hub_cap);
     const uint32_t n_reg = *reinterpret_cast<volatile unsigned *>(&c->g_items[cur]);
-    if (a.box != nullptr) {
+    if (GQ == 64 || a.box == nullptr) {
+      if (n_hub + n_reg == 0u) break;
+    } else if constexpr (GQ != 64) {
       // ---- serve mode: RETIRE lanes whose query has no pending work left, then
       //      ADMIT the mailbox's new requests into free lanes (next round) ----
       const uint32_t *gact_c = a.gact + (size_t)cur * a.ngroups;
@@ -351,8 +438,6 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
         const bool stop = ld_volatile_sys(&a.box->stop) != 0u;
         if (lane == 0) c->g_exit = (stop || (n_hub + n_reg == 0u && busy == 0u && admitted == 0u)) ? 1u : 0u;
       }
-    } else if (n_hub + n_reg == 0u) {
-      break;
     }
     if (a.box == nullptr && round >= a.max_rounds) {
       if (threadIdx.x == 0) raise_status(c, FG_ERR_TIMEOUT, kSiteRounds);
@@ -379,7 +464,7 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
           if (ld_volatile_i32(&c->abort)) idx = n_hub + n_reg;
         }
         idx = __shfl_sync(kFull, idx, 0);
-        ItemDesc d{kItemEnd, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        ItemDesc d{kItemEnd, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0ull};
         if (idx < n_hub) {
           const uint4 itm = __ldcg(a.items + idx);
           const uint32_t e1 = G.rp[itm.y + 1];
@@ -389,19 +474,21 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
           d.eb = itm.z;
           d.ee = itm.z + a.hub_chunk < e1 ? itm.z + a.hub_chunk : e1;
           d.m = itm.w;
+          if constexpr (GQ == 64) d.m |= (unsigned long long)__ldcg(a.hub_hi + idx) << 32;
           d.n = (d.ee - d.eb + 31u) / 32u;
         } else if (idx < n_hub + n_reg) {
           const uint32_t key = __ldcg(a.items + a.hub_cap + (idx - n_hub)).x;
           const uint32_t grp = key / (uint32_t)G.nparts, p = key - grp * (uint32_t)G.nparts;
           const uint32_t base = p << G.slog2;
-          uint32_t *pm_g = pend_c + (size_t)grp * row + base;
-          uint32_t *rp_s = buf_rp(k), *pm_s = buf_pm(k), *vid_s = buf_vid(k), *pre_s = buf_pre(k);
+          M *pm_g = pend_c + (size_t)grp * row + base;
+          uint32_t *rp_s = buf_rp(k), *vid_s = buf_vid(k);
+          M *pm_s = buf_pm(k);
           // stage the row offsets and the group's pending masks (one bulk
           // phase; the expected bytes are announced before the copies); the
           // buffer's previous readers are done (empty barrier), so the proxy
           // fence orders their reads before the bulk writes
           if (lane == 0) {
-            const uint32_t b_rp = (uint32_t)(S + 4) * 4u, b_pm = (uint32_t)S * 4u;
+            const uint32_t b_rp = (uint32_t)(S + 4) * 4u, b_pm = (uint32_t)S * (uint32_t)sizeof(M);
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&s_tma[k], b_rp + b_pm);
             bulk_g2s(rp_s, G.rp + base, b_rp, &s_tma[k]);
@@ -426,23 +513,17 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
             if (__any_sync(kFull, bad) && lane == 0) raise_status(c, FG_ERR_CUDA, kSiteStageCheck);
           }
           // this round's masks of the item are taken: clear them for reuse
-          for (int i = lane; i < (S >> 2); i += 32) reinterpret_cast<uint4 *>(pm_g)[i] = make_uint4(0u, 0u, 0u, 0u);
-          // list the pending vertices with an arc, and the prefix of their arcs
-          uint32_t cnt = 0, arcs = 0;
+          for (int i = lane; i < ((S * MW) >> 2); i += 32)
+            reinterpret_cast<uint4 *>(pm_g)[i] = make_uint4(0u, 0u, 0u, 0u);
+          // list the pending vertices with an arc
+          uint32_t cnt = 0;
           for (int i0 = 0; i0 < S; i0 += 32) {
             const int i = i0 + lane;
             const uint32_t deg = rp_s[i + 1] - rp_s[i];
             const bool keep = pm_s[i] != 0u && deg > 0u;
             const unsigned bm = __ballot_sync(kFull, keep);
-            const uint32_t dk = keep ? deg : 0u;
-            const uint32_t incl = warp_incl_scan(dk);
-            if (keep) {
-              const uint32_t pos = cnt + (uint32_t)__popc(bm & ((1u << lane) - 1u));
-              vid_s[pos] = (uint32_t)i;
-              pre_s[pos] = arcs + incl - dk;
-            }
+            if (keep) vid_s[cnt + (uint32_t)__popc(bm & ((1u << lane) - 1u))] = (uint32_t)i;
             cnt += (uint32_t)__popc(bm);
-            arcs += __shfl_sync(kFull, incl, 31);
           }
           d.kind = kItemPart;
           d.grp = grp;
@@ -476,9 +557,9 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
           break;
         }
         uint32_t *Dg = a.D + (size_t)d.grp * row * (size_t)Gq;
-        uint32_t *Dg_g = Dg + g;
+        uint32_t *Dg_g = Dg + (GQ == 64 ? 2 * lane : g);  // this lane's value (G = 64: pair) of vertex 0
         uint32_t gacc = 0u;  // lanes this warp marked pending for the next round (serve mode)
-        uint32_t *pend_g = pend_n + (size_t)d.grp * row;
+        M *pend_g = pend_n + (size_t)d.grp * row;
         uint32_t *dirty_g = dirty_n + (size_t)d.grp * G.nparts;
         uint32_t *gb_n = a.gbest ? a.gbest + (size_t)nxt * a.ngroups + d.grp : nullptr;
         // Steps of 32 arcs, lane l holding arc l. Two steps ahead of the one
@@ -486,7 +567,7 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
         // it asks L2 for the arc's target line (prefetch.global.L2), so the
         // relaxation's loads of target values find their lines on chip
         // without holding registers while they travel.
-        auto run = [&](uint32_t nsteps, auto make, const uint32_t *sdv_g, uint32_t dv_own, bool chk) {
+        auto run = [&](uint32_t nsteps, auto make, auto sdv_g, auto dv_own, bool chk) {
           const uint4 none = make_uint4(0u, 1u, kNoArc, 0u);
           uint4 a0 = make(0u);
           uint4 a1 = nsteps > 1u ? make(1u) : none;
@@ -496,26 +577,47 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
             __syncwarp();
             if (a1.z != kNoArc) prefetch_l2(Dg + ((size_t)a1.x << LG));
             const uint4 a2 = i + 2u < nsteps ? make(i + 2u) : none;
-            g_step<QT, GQ>(a, sarc, sdv_g, dv_own, Dg_g, pend_g, dirty_g, gb_n, g, h, i32, gacc, chk);
+            if constexpr (GQ == 64)
+              g_step64<QT>(a, sarc, sdv_g, dv_own, Dg_g, pend_g, dirty_g, lane, i32, chk);
+            else
+              g_step<QT, GQ>(a, sarc, sdv_g, dv_own, Dg_g, pend_g, dirty_g, gb_n, g, h, i32, gacc, chk);
             __syncwarp();  // sarc is rewritten by the next step
             a0 = a1;
             a1 = a2;
           }
         };
         if (d.kind == kItemHub) {
-          uint32_t dv = kInf;
-          if (((d.m >> g) & 1u) != 0u) dv = __ldcg(Dg_g + ((size_t)d.pv << LG));
-          // a sum can reach 2^32 - 1 only from a value within max_w of it
-          const bool chk_hub = __any_sync(kFull, dv != kInf && dv >= ovf_lim);
+          // this lane's value(s) of the hub, kInf where not pending
+          using V = std::conditional_t<GQ == 64, uint2, uint32_t>;
+          V dv;
+          uint32_t nact;  // values of this lane that relax the chunk
+          bool near;      // a sum can reach 2^32 - 1 only from a value within max_w of it
+          if constexpr (GQ == 64) {
+            const bool p0 = ((d.m >> lane) & 1ull) != 0ull, p1 = ((d.m >> (32 + lane)) & 1ull) != 0ull;
+            dv = make_uint2(kInf, kInf);
+            if (p0 || p1) {
+              const uint2 t = __ldcg(reinterpret_cast<const uint2 *>(Dg_g + ((size_t)d.pv << LG)));
+              if (p0) dv.x = t.x;
+              if (p1) dv.y = t.y;
+            }
+            nact = (dv.x != kInf ? 1u : 0u) + (dv.y != kInf ? 1u : 0u);
+            near = (dv.x != kInf && dv.x >= ovf_lim) || (dv.y != kInf && dv.y >= ovf_lim);
+          } else {
+            dv = kInf;
+            if (((d.m >> g) & 1ull) != 0ull) dv = __ldcg(Dg_g + ((size_t)d.pv << LG));
+            nact = dv != kInf ? 1u : 0u;
+            near = dv != kInf && dv >= ovf_lim;
+          }
+          const bool chk_hub = __any_sync(kFull, near);
           for (;;) {
             uint32_t s0 = 0;
             if (lane == 0) s0 = atomicAdd(&s_desc[k].next, 4u);  // four steps of 32 arcs at a time
             s0 = __shfl_sync(kFull, s0, 0);
             if (s0 >= d.n) break;
             const uint32_t ns = d.n - s0 < 4u ? d.n - s0 : 4u;
-            if (dv != kInf) {  // this lane relaxes every arc of the claimed steps
+            if (nact != 0u) {  // this lane relaxes every arc of the claimed steps
               const uint32_t e_lo = d.eb + s0 * 32u, e_hi = d.eb + (s0 + ns) * 32u;
-              r32 += (e_hi < d.ee ? e_hi : d.ee) - e_lo;
+              r32 += nact * ((e_hi < d.ee ? e_hi : d.ee) - e_lo);
             }
             auto make = [&](uint32_t i) {
               const uint32_t e = d.eb + (s0 + i) * 32u + (uint32_t)lane;
@@ -525,11 +627,12 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
                                 (has && QT != Q_BFS && G.wt != nullptr) ? __ldg(G.wt + e) : 1u,
                                 has ? 0u : kNoArc, 0u);
             };
-            run(ns, make, nullptr, dv, chk_hub);
+            run(ns, make, static_cast<const V *>(nullptr), dv, chk_hub);
           }
         } else {
           const uint32_t base = d.pv << G.slog2;
-          const uint32_t *rp_s = buf_rp(k), *pm_s = buf_pm(k), *vid_s = buf_vid(k);
+          const uint32_t *rp_s = buf_rp(k), *vid_s = buf_vid(k);
+          const M *pm_s = buf_pm(k);
           const uint32_t bound =
               (a.window != 0u && a.gbest != nullptr)
                   ? sat_add_u32(__ldcg(a.gbest + (size_t)cur * a.ngroups + d.grp), a.window)
@@ -542,7 +645,7 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
             const uint32_t j = b0 + (uint32_t)lane;
             const bool valid = j < d.n;
             const uint32_t li = valid ? vid_s[j] : 0u;
-            const uint32_t m = valid ? pm_s[li] : 0u;
+            const M m = valid ? pm_s[li] : (M)0u;
             const uint32_t a0 = valid ? rp_s[li] : 0u;
             const uint32_t deg = valid ? rp_s[li + 1] - a0 : 0u;
             const uint32_t incl = warp_incl_scan(deg);
@@ -554,6 +657,26 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
             // pending. Under a window, values at or beyond the group's bound
             // stay pending for a later round (Delta-stepping across rounds).
             bool big = false;  // some source value within max_w of 2^32 - 1 (sums need the check)
+            if constexpr (GQ == 64) {
+              // pairs: row L of the [32][32] pair table, lane l = queries 2l, 2l + 1
+              uint2 *sdv2 = reinterpret_cast<uint2 *>(sdv);
+#pragma unroll 4
+              for (int L = 0; L < 32; ++L) {
+                const uint32_t vL = __shfl_sync(kFull, li, L);
+                const M mL = __shfl_sync(kFull, m, L);
+                const bool p0 = ((mL >> lane) & 1ull) != 0ull, p1 = ((mL >> (32 + lane)) & 1ull) != 0ull;
+                uint2 dd = make_uint2(kInf, kInf);
+                if (p0 || p1) {
+                  const uint2 t = __ldcg(reinterpret_cast<const uint2 *>(Dg_g + ((size_t)(base + vL) << LG)));
+                  if (p0) dd.x = t.x;
+                  if (p1) dd.y = t.y;
+                }
+                sdv2[(L << 5) + lane] = dd;
+                big |= (dd.x != kInf && dd.x >= ovf_lim) || (dd.y != kInf && dd.y >= ovf_lim);
+                const uint32_t degL = __shfl_sync(kFull, deg, L);
+                r32 += degL * ((dd.x != kInf ? 1u : 0u) + (dd.y != kInf ? 1u : 0u));
+              }
+            } else {
 #pragma unroll 4
             for (int L0 = 0; L0 < 32; L0 += SL) {
               const int L = L0 + h;
@@ -581,6 +704,7 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
               const uint32_t degL = __shfl_sync(kFull, deg, L);
               if (dd != kInf) r32 += degL;  // this lane relaxes every arc of vertex L
             }
+            }
             __syncwarp();
             auto make = [&](uint32_t i) {
               const uint32_t t = i * 32u + (uint32_t)lane;
@@ -592,7 +716,11 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
                                 (has && QT != Q_BFS && G.wt != nullptr) ? __ldg(G.wt + eL) : 1u,
                                 has ? (uint32_t)L : kNoArc, 0u);
             };
-            run((tot + 31u) / 32u, make, sdv + g, kInf, __any_sync(kFull, big));
+            if constexpr (GQ == 64)
+              run((tot + 31u) / 32u, make, static_cast<const uint2 *>(reinterpret_cast<uint2 *>(sdv) + lane),
+                  make_uint2(kInf, kInf), __any_sync(kFull, big));
+            else
+              run((tot + 31u) / 32u, make, static_cast<const uint32_t *>(sdv + g), kInf, __any_sync(kFull, big));
             __syncwarp();  // sdv is rewritten by the next batch
           }
         }
@@ -600,7 +728,7 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
         n_improved += i32;
         r32 = 0u;
         i32 = 0u;
-        if (a.gact != nullptr) {
+        if (GQ != 64 && a.gact != nullptr) {
           gacc = __reduce_or_sync(kFull, gacc);
           if (lane == 0 && gacc != 0u) atomicOr(a.gact + (size_t)nxt * a.ngroups + d.grp, gacc);
         }
@@ -642,7 +770,7 @@ done:
 __global__ void __launch_bounds__(256) group_out_kernel(const uint32_t *D, uint32_t *out, const int32_t *orig,
                                                         const int32_t *rowmap, int64_t n, int64_t npad, int32_t G,
                                                         int32_t glog2, int32_t nq, int64_t tiles_per_group) {
-  __shared__ uint32_t t[32][33];
+  __shared__ uint32_t t[64][33];
   const int64_t grp = blockIdx.x / tiles_per_group;
   const int64_t v0 = (blockIdx.x % tiles_per_group) * 32;
   const uint32_t *src = D + ((size_t)grp * (size_t)npad + (size_t)v0) * (size_t)G;
@@ -714,10 +842,12 @@ static const void *group_fn(int qtype, int G) {
   if (qtype == Q_BFS) {
     if (G == 8) return (const void *)group_kernel<Q_BFS, 8>;
     if (G == 16) return (const void *)group_kernel<Q_BFS, 16>;
+    if (G == 64) return (const void *)group_kernel<Q_BFS, 64>;
     return (const void *)group_kernel<Q_BFS, 32>;
   }
   if (G == 8) return (const void *)group_kernel<Q_SSSP, 8>;
   if (G == 16) return (const void *)group_kernel<Q_SSSP, 16>;
+  if (G == 64) return (const void *)group_kernel<Q_SSSP, 64>;
   return (const void *)group_kernel<Q_SSSP, 32>;
 }
 

@@ -153,8 +153,8 @@ struct fg_graph {
   fg::DevBuf hubs;
   int32_t nhubs = 0;
   uint64_t hub_chunks = 0;
-  int group_blocks[3] = {0, 0, 0}, group_threads[3] = {0, 0, 0};
-  size_t group_smem[3] = {0, 0, 0};
+  int group_blocks[4] = {0, 0, 0, 0}, group_threads[4] = {0, 0, 0, 0};
+  size_t group_smem[4] = {0, 0, 0, 0};
 };
 
 namespace fg {

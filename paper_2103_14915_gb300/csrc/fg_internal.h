@@ -117,15 +117,16 @@ struct GroupArgs {
   DevGraph g;
   int qtype = Q_SSSP;
   int32_t nq = 0;
-  int32_t G = 16;                 // queries per group: 8, 16 or 32
+  int32_t G = 16;                 // queries per group: 8, 16, 32 or 64
   int32_t glog2 = 4;              // log2(G)
   int32_t ngroups = 0;            // ceil(nq / G)
   int64_t npad = 0;               // nparts * S: vertices per group row, padded to whole partitions
   const int32_t *src = nullptr;   // [nq] original ids (device)
   uint32_t *D = nullptr;          // [ngroups][npad][G]
-  uint32_t *pend = nullptr;       // [2][ngroups][npad] G-bit masks
+  uint32_t *pend = nullptr;       // [2][ngroups][npad] G-bit masks (32-bit words; 64-bit for G = 64)
   uint32_t *dirty = nullptr;      // [2][ngroups * nparts]
   uint4 *items = nullptr;         // [hub_cap + ngroups * nparts]
+  uint32_t *hub_hi = nullptr;     // [hub_cap] G = 64: upper mask word of each hub-chunk item
   uint32_t hub_cap = 0;           // item slots reserved for hub chunks
   const uint32_t *hubs = nullptr; // [nhubs] internal ids of the hubs (vertices with many arcs)
   int32_t nhubs = 0;

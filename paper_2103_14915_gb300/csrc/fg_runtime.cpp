@@ -470,8 +470,8 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
   if (o.host_io < 0 || o.host_io > 2) return fail(FG_ERR_INVALID_ARG, "host_io must be 0, 1 or 2");
   if (o.threads_per_vertex != 0 && o.threads_per_vertex != 1 && o.threads_per_vertex != 32)
     return fail(FG_ERR_INVALID_ARG, "threads_per_vertex must be 0, 1 or 32");
-  if (o.group != 0 && o.group != 1 && o.group != 8 && o.group != 16 && o.group != 32)
-    return fail(FG_ERR_INVALID_ARG, "group must be 0, 1, 8, 16 or 32");
+  if (o.group != 0 && o.group != 1 && o.group != 8 && o.group != 16 && o.group != 32 && o.group != 64)
+    return fail(FG_ERR_INVALID_ARG, "group must be 0, 1, 8, 16, 32 or 64");
   if (o.group_order != 0 && o.group_order != 1) return fail(FG_ERR_INVALID_ARG, "group_order must be 0 or 1");
   if (o.check_staging != 0 && o.check_staging != 1) return fail(FG_ERR_INVALID_ARG, "check_staging must be 0 or 1");
   if (qtype == Q_PPR) o.sched = FG_SCHED_FIFO;  // PPR buffers are scheduled first-in first-out
@@ -566,8 +566,9 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
       CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
       const size_t held = ws.g_D.bytes + ws.g_pend.bytes + ws.g_dirty.bytes + ws.g_items.bytes + ws.g_best.bytes;
       const double avail = 0.9 * (double)(free_b + held) - 512.0 * 1024 * 1024;
-      const double per_group = (double)npad * 4.0 * (double)Gq + 8.0 * (double)npad + 24.0 * (double)g->nparts +
-                               16.0 * (double)g->hub_chunks + 8.0;
+      const double mask_b = Gq == 64 ? 8.0 : 4.0;
+      const double per_group = (double)npad * 4.0 * (double)Gq + 2.0 * mask_b * (double)npad +
+                               24.0 * (double)g->nparts + 20.0 * (double)g->hub_chunks + 8.0;
       int64_t cap_groups = std::max<int64_t>(1, (int64_t)(avail / per_group));
       const int64_t key_cap = (int64_t)(0xFFFFFFF0ull / (uint64_t)g->nparts);
       cap_groups = std::min<int64_t>(cap_groups, key_cap);
@@ -575,6 +576,8 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
       nbq = std::min<int64_t>(nbq, nq);
     }
     const int gi = glog2 - 3;
+    if (Gq == 64 && qtype == Q_SSSP && o.sched == FG_SCHED_PRIORITY && o.sched_window != 0u)
+      return fail(FG_ERR_UNSUPPORTED, "the group engine has no window for groups of 64; use FIFO or a group of 32");
     if (!group_fits(g->S, Gq))
       return fail(FG_ERR_UNSUPPORTED, "group %d does not fit shared memory with partitions of %d vertices", Gq, g->S);
     if (g->group_blocks[gi] == 0)
@@ -585,9 +588,11 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
     if (hub_cap + (uint64_t)ngroups_max * (uint64_t)g->nparts >= 0xFFFFFFFFull)
       return fail(FG_ERR_UNSUPPORTED, "too many work items for one launch; lower query_batch");
     CUDA_TRY(ws.g_D.reserve(4 * (size_t)ngroups_max * (size_t)npad * (size_t)Gq));
-    CUDA_TRY(ws.g_pend.reserve(8 * (size_t)ngroups_max * (size_t)npad));
+    CUDA_TRY(ws.g_pend.reserve((Gq == 64 ? 16 : 8) * (size_t)ngroups_max * (size_t)npad));
     CUDA_TRY(ws.g_dirty.reserve(8 * (size_t)ngroups_max * (size_t)g->nparts));
-    CUDA_TRY(ws.g_items.reserve(16 * (size_t)(hub_cap + (uint64_t)ngroups_max * (uint64_t)g->nparts)));
+    // work items, then (G = 64) the upper mask words of the hub-chunk items
+    CUDA_TRY(ws.g_items.reserve(16 * (size_t)(hub_cap + (uint64_t)ngroups_max * (uint64_t)g->nparts) +
+                                (Gq == 64 ? 4 * (size_t)hub_cap : 0)));
     CUDA_TRY(ws.g_best.reserve(8 * (size_t)ngroups_max));
     CUDA_TRY(ws.ctrl.reserve(sizeof(Ctrl)));
     d_ctrl = ws.ctrl.as<Ctrl>();
@@ -623,6 +628,8 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
       a.dirty = ws.g_dirty.as<uint32_t>();
       a.items = ws.g_items.as<uint4>();
       a.hub_cap = (uint32_t)((uint64_t)a.ngroups * g->hub_chunks);
+      a.hub_hi = Gq == 64 ? reinterpret_cast<uint32_t *>(a.items + a.hub_cap + (size_t)a.ngroups * (size_t)g->nparts)
+                          : nullptr;
       a.hubs = g->nhubs ? g->hubs.as<uint32_t>() : nullptr;
       a.nhubs = g->nhubs;
       a.hub_chunk = kHubChunk;

@@ -122,7 +122,7 @@ extern "C" fg_status fg_tune_opts_ex(fg_graph *g, int32_t kind, const int32_t *s
   // the query group (the default resolves to 16 on cut-dominated graphs, else 1)
   const int auto_group = (g->m > 0 && 2 * g->cut > g->m) ? 16 : 1;
   if (kind != FG_QUERY_PPR) {
-    for (int G : {1, 16, 32}) {
+    for (int G : {1, 16, 32, 64}) {
       if (G == auto_group || (G > 1 && !group_fits(g->S, G))) continue;
       fg_opts o = base;
       o.group = G;
@@ -132,7 +132,7 @@ extern "C" fg_status fg_tune_opts_ex(fg_graph *g, int32_t kind, const int32_t *s
   }
   if (kind != FG_QUERY_PPR && pick.group > 1) {
     // group engine: a per-group window (Delta-stepping across rounds) for SSSP
-    if (kind == FG_QUERY_SSSP && g->weighted) {
+    if (kind == FG_QUERY_SSSP && g->weighted && pick.group != 64) {  // groups of 64 run FIFO rounds only
       const fg_opts chosen = pick;
       for (double f : {16.0, 4.0}) {
         fg_opts o = chosen;

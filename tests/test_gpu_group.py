@@ -80,7 +80,7 @@ def create(g, method=fg.FG_PART_AUTO, S=0):
 
 
 @pytest.mark.parametrize("gi", range(len(GRAPHS)), ids=[g.name or f"g{i}" for i, g in enumerate(GRAPHS)])
-@pytest.mark.parametrize("G", [8, 16, 32])
+@pytest.mark.parametrize("G", [8, 16, 32, 64])
 def test_group_engine_exact(gi, G):
     g = GRAPHS[gi]
     h = create(g, fg.FG_PART_RANGE, 64)
@@ -173,11 +173,14 @@ def test_group_option_is_checked_on_the_host():
         s_d = torch.zeros(1, dtype=torch.int32, device=DEV)
         out = torch.empty((1, g.n), dtype=torch.int32, device=DEV)
         assert fg.fg_sssp_batch(h, s_d, 1, out, None, fg.fg_default_opts(group=12)) == fg.FG_ERR_INVALID_ARG
+        # groups of 64 run FIFO rounds only
+        o = fg.fg_default_opts(group=64, sched=fg.FG_SCHED_PRIORITY, sched_window=16)
+        assert fg.fg_sssp_batch(h, s_d, 1, out, None, o) == fg.FG_ERR_UNSUPPORTED
     finally:
         fg.fg_graph_destroy(h)
 
 
-@pytest.mark.parametrize("G", [8, 32])
+@pytest.mark.parametrize("G", [8, 32, 64])
 def test_group_order_keeps_rows(G):
     """Queries are regrouped by two-hop reach inside the library; every row still
     belongs to its own source, with duplicates, hubs, isolated vertices and
@@ -222,10 +225,30 @@ def test_staging_self_check_is_clean():
         h = create(g, method, S)
         try:
             srcs = inputs.sources_uniform(g, 40, 5)
-            for G in (8, 16, 32):
+            for G in (8, 16, 32, 64):
                 for kind in ("sssp", "bfs"):
                     got = run(h, g, kind, srcs, group=G, check_staging=1)
                     ref = oracle.sssp(g, srcs) if kind == "sssp" else oracle.bfs(g, srcs)
                     assert np.array_equal(got, ref), (g.name, G, kind)
         finally:
             fg.fg_graph_destroy(h)
+
+
+def test_group_64_split_batches_and_hub_masks():
+    """Groups of 64: 64-bit pending masks (query 2l + j at bit 32j + l), hub
+    chunks whose lanes span both mask words, and a batch split into launches
+    whose last group is partial."""
+    g = hub_graph()
+    h = create(g, fg.FG_PART_RANGE, 128)
+    try:
+        deg = np.diff(g.row_ptr)
+        hubs = np.flatnonzero(deg > 512)
+        srcs = inputs.sources_uniform(g, 150, 9).astype(np.int32)
+        srcs[::7] = hubs[np.arange(len(srcs[::7])) % len(hubs)]  # hubs in both halves of several groups
+        for kind in ("sssp", "bfs"):
+            ref = oracle.sssp(g, srcs) if kind == "sssp" else oracle.bfs(g, srcs)
+            for qb in (0, 70):
+                got = run(h, g, kind, srcs, group=64, query_batch=qb)
+                assert np.array_equal(got, ref), (kind, qb)
+    finally:
+        fg.fg_graph_destroy(h)
