@@ -47,6 +47,7 @@ namespace fg {
 constexpr int kGCons = 8;                    // consumer warps per block
 constexpr int kGThreads = (kGCons + 1) * 32;  // and one producer warp
 constexpr int kGUnroll = 8;                  // arc slots per lane group with loads in flight at once
+constexpr int kGUnroll64 = 8;                // the same for groups of 64 (two values per lane)
 
 enum : uint32_t { kItemPart = 0, kItemHub = 1, kItemEnd = 2 };
 
@@ -86,13 +87,17 @@ __host__ __device__ __forceinline__ typename GroupLanes<GQ>::M group_bit(uint32_
 
 // Shared memory: two item buffers (row offsets, pending masks of one or two
 // words, listed vertices), then per consumer warp the current step's 32 arcs
-// (uint4 each) and one [32][G] table of source values.
+// (uint4 each) and one [B][G] table of source values, B = the listed
+// vertices a warp takes at a time (32; 16 for G = 64, so that three blocks
+// fit an SM).
+__host__ __device__ constexpr int group_batch(int G) { return G == 64 ? 16 : 32; }
 __host__ __device__ inline size_t group_mask_words(int G) { return G == 64 ? 2u : 1u; }
 __host__ __device__ inline size_t group_item_words(int S, int G) {
   return (size_t)(S + 4) + (size_t)S * (1u + group_mask_words(G));
 }
 __host__ __device__ inline size_t group_smem_bytes(int S, int G) {
-  return (2 * group_item_words(S, G) + (size_t)kGCons * (128u + 32u * (size_t)G)) * sizeof(uint32_t);
+  return (2 * group_item_words(S, G) + (size_t)kGCons * (128u + (size_t)group_batch(G) * (size_t)G)) *
+         sizeof(uint32_t);
 }
 
 __device__ __forceinline__ uint32_t g_relax(Ctrl *c, uint32_t d, uint32_t w) {
@@ -179,11 +184,11 @@ __device__ __forceinline__ void g_step64(const GroupArgs &a, const uint4 *sarc, 
                                          uint32_t &improved, bool chk) {
   const int slog2 = a.g.slog2;
 #pragma unroll 1
-  for (int j0 = 0; j0 < 32; j0 += kGUnroll) {
-    uint2 nd[kGUnroll], cur[kGUnroll];
-    bool act0[kGUnroll], act1[kGUnroll];
+  for (int j0 = 0; j0 < 32; j0 += kGUnroll64) {
+    uint2 nd[kGUnroll64], cur[kGUnroll64];
+    bool act0[kGUnroll64], act1[kGUnroll64];
 #pragma unroll
-    for (int q = 0; q < kGUnroll; ++q) {
+    for (int q = 0; q < kGUnroll64; ++q) {
       const uint4 e = sarc[j0 + q];  // one broadcast read
       uint2 dv = make_uint2(kInf, kInf);
       if (e.z != kNoArc) dv = sdv2 != nullptr ? sdv2[e.z << 5] : dv_own;
@@ -205,7 +210,7 @@ __device__ __forceinline__ void g_step64(const GroupArgs &a, const uint4 *sarc, 
       cur[q] = (act0[q] || act1[q]) ? *reinterpret_cast<const uint2 *>(Dg_p + ((size_t)e.x << 6)) : make_uint2(0u, 0u);
     }
 #pragma unroll
-    for (int q = 0; q < kGUnroll; ++q) {
+    for (int q = 0; q < kGUnroll64; ++q) {
       const bool i0 = act0[q] && nd[q].x < cur[q].x, i1 = act1[q] && nd[q].y < cur[q].y;
       const uint32_t uq = sarc[j0 + q].x;  // read again rather than held in a register
       uint32_t *t = Dg_p + ((size_t)uq << 6);
@@ -222,10 +227,13 @@ __device__ __forceinline__ void g_step64(const GroupArgs &a, const uint4 *sarc, 
 }
 
 template <int QT, int GQ>
-__global__ void __launch_bounds__(kGThreads, GQ == 64 ? 2 : 3) group_kernel(GroupArgs a) {
+__global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
   extern __shared__ __align__(16) uint32_t g_smem[];
   __shared__ __align__(8) uint64_t s_full[2], s_empty[2], s_tma[2];
   __shared__ ItemDesc s_desc[2];
+  // block counters (lane relaxations, improvements, arcs read, visits) and
+  // block 0's phase clock, kept out of the registers of every thread
+  __shared__ unsigned long long s_stat[4], s_ph[6], s_tprev;
   const int lane = lane_id(), wid = threadIdx.x >> 5;
   const bool producer = wid == kGCons;
   const DevGraph &G = a.g;
@@ -245,25 +253,26 @@ __global__ void __launch_bounds__(kGThreads, GQ == 64 ? 2 : 3) group_kernel(Grou
   auto buf_vid = [&](uint32_t k) { return g_smem + k * iw + (S + 4) + MW * S; };
   // per consumer warp: the step's arcs (uint4[32]) and the batch's source values ([32][G])
   uint4 *sarc = reinterpret_cast<uint4 *>(g_smem + 2 * iw) + (size_t)(producer ? 0 : wid) * 32u;
-  uint32_t *sdv = g_smem + 2 * iw + (size_t)kGCons * 128u + (size_t)(producer ? 0 : wid) * 32u * (uint32_t)Gq;
+  constexpr int kB = group_batch(GQ);  // listed vertices per consumer batch
+  uint32_t *sdv = g_smem + 2 * iw + (size_t)kGCons * 128u + (size_t)(producer ? 0 : wid) * (size_t)kB * (uint32_t)Gq;
   Ctrl *c = a.ctrl;
   unsigned gen = *reinterpret_cast<volatile unsigned *>(&c->bar_gen);
   uint32_t it_base = 0;   // items this block has gone through (both buffers), the same in every warp
   uint32_t tma_bits = 0;  // producer: phase parity of s_tma[0] (bit 0) and s_tma[1] (bit 1)
-  unsigned long long n_relaxed = 0, n_improved = 0, n_visits = 0, n_arcs = 0;
-  uint32_t r32 = 0, i32 = 0;  // per-batch counters, folded into the 64-bit ones after each batch
-  uint64_t t_prev = (blockIdx.x == 0 && threadIdx.x == 0) ? global_ns() : 0ull;
-  unsigned long long ph[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+  uint32_t r32 = 0, i32 = 0, a32 = 0;  // per-item counters, folded into s_stat after each item
 #define FG_GPHASE(k)                                            \
   do {                                                          \
     if (blockIdx.x == 0 && threadIdx.x == 0) {                  \
       const uint64_t t_now = global_ns();                       \
-      ph[k] += t_now - t_prev;                                  \
-      t_prev = t_now;                                           \
+      s_ph[k] += t_now - s_tprev;                               \
+      s_tprev = t_now;                                          \
     }                                                           \
   } while (0)
 
   if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) s_stat[k] = 0ull;
+    for (int k = 0; k < 6; ++k) s_ph[k] = 0ull;
+    s_tprev = global_ns();
     for (int k = 0; k < 2; ++k) {
       mbar_init(&s_full[k], 1);
       mbar_init(&s_empty[k], kGCons);
@@ -532,7 +541,7 @@ __global__ void __launch_bounds__(kGThreads, GQ == 64 ? 2 : 3) group_kernel(Grou
         }
         if (lane == 0) {
           s_desc[k] = d;
-          if (d.kind != kItemEnd) ++n_visits;
+          if (d.kind != kItemEnd) s_stat[3] += 1ull;  // the producer's lane 0 alone counts visits
         }
         __syncwarp();  // every lane's list writes precede the publishing arrival
         if (lane == 0) mbar_arrive(&s_full[k]);
@@ -622,7 +631,7 @@ __global__ void __launch_bounds__(kGThreads, GQ == 64 ? 2 : 3) group_kernel(Grou
             auto make = [&](uint32_t i) {
               const uint32_t e = d.eb + (s0 + i) * 32u + (uint32_t)lane;
               const bool has = e < d.ee;
-              n_arcs += has ? 1ull : 0ull;
+              a32 += has ? 1u : 0u;
               return make_uint4(has ? __ldg(G.adj + e) : 0u,
                                 (has && QT != Q_BFS && G.wt != nullptr) ? __ldg(G.wt + e) : 1u,
                                 has ? 0u : kNoArc, 0u);
@@ -639,11 +648,11 @@ __global__ void __launch_bounds__(kGThreads, GQ == 64 ? 2 : 3) group_kernel(Grou
                   : kInf;
           for (;;) {
             uint32_t b0 = 0;
-            if (lane == 0) b0 = atomicAdd(&s_desc[k].next, 32u);
+            if (lane == 0) b0 = atomicAdd(&s_desc[k].next, (uint32_t)kB);
             b0 = __shfl_sync(kFull, b0, 0);
             if (b0 >= d.n) break;
             const uint32_t j = b0 + (uint32_t)lane;
-            const bool valid = j < d.n;
+            const bool valid = lane < kB && j < d.n;
             const uint32_t li = valid ? vid_s[j] : 0u;
             const M m = valid ? pm_s[li] : (M)0u;
             const uint32_t a0 = valid ? rp_s[li] : 0u;
@@ -658,10 +667,10 @@ __global__ void __launch_bounds__(kGThreads, GQ == 64 ? 2 : 3) group_kernel(Grou
             // stay pending for a later round (Delta-stepping across rounds).
             bool big = false;  // some source value within max_w of 2^32 - 1 (sums need the check)
             if constexpr (GQ == 64) {
-              // pairs: row L of the [32][32] pair table, lane l = queries 2l, 2l + 1
+              // pairs: row L of the [16][32] pair table, lane l = queries 2l, 2l + 1
               uint2 *sdv2 = reinterpret_cast<uint2 *>(sdv);
 #pragma unroll 4
-              for (int L = 0; L < 32; ++L) {
+              for (int L = 0; L < kB; ++L) {
                 const uint32_t vL = __shfl_sync(kFull, li, L);
                 const M mL = __shfl_sync(kFull, m, L);
                 const bool p0 = ((mL >> lane) & 1ull) != 0ull, p1 = ((mL >> (32 + lane)) & 1ull) != 0ull;
@@ -711,7 +720,7 @@ __global__ void __launch_bounds__(kGThreads, GQ == 64 ? 2 : 3) group_kernel(Grou
               const bool has = t < tot;
               const int L = owner_lane(exd, has ? t : 0u);
               const uint32_t eL = __shfl_sync(kFull, a0, L) + (t - __shfl_sync(kFull, exd, L));
-              n_arcs += has ? 1ull : 0ull;
+              a32 += has ? 1u : 0u;
               return make_uint4(has ? __ldg(G.adj + eL) : 0u,
                                 (has && QT != Q_BFS && G.wt != nullptr) ? __ldg(G.wt + eL) : 1u,
                                 has ? (uint32_t)L : kNoArc, 0u);
@@ -724,10 +733,18 @@ __global__ void __launch_bounds__(kGThreads, GQ == 64 ? 2 : 3) group_kernel(Grou
             __syncwarp();  // sdv is rewritten by the next batch
           }
         }
-        n_relaxed += r32;
-        n_improved += i32;
+        {
+          const unsigned long long r = warp_sum((unsigned long long)r32), im = warp_sum((unsigned long long)i32),
+                                   ar = warp_sum((unsigned long long)a32);
+          if (lane == 0) {
+            atomicAdd(&s_stat[0], r);
+            atomicAdd(&s_stat[1], im);
+            atomicAdd(&s_stat[2], ar);
+          }
+        }
         r32 = 0u;
         i32 = 0u;
+        a32 = 0u;
         if (GQ != 64 && a.gact != nullptr) {
           gacc = __reduce_or_sync(kFull, gacc);
           if (lane == 0 && gacc != 0u) atomicOr(a.gact + (size_t)nxt * a.ngroups + d.grp, gacc);
@@ -747,19 +764,16 @@ __global__ void __launch_bounds__(kGThreads, GQ == 64 ? 2 : 3) group_kernel(Grou
   }
 done:
 #undef FG_GPHASE
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ph[2] += global_ns() - t_prev;
-    for (int k = 0; k < 6; ++k) atomicAdd(&c->phase_ns[k], ph[k]);
-  }
-  {
-    const unsigned long long r = warp_sum(n_relaxed), im = warp_sum(n_improved), ar = warp_sum(n_arcs);
-    const unsigned long long vi = warp_sum(n_visits);
-    if (lane == 0) {
-      atomicAdd(&c->edges, r);
-      atomicAdd(&c->ops, im);
-      atomicAdd(&c->arcs_read, ar);
-      atomicAdd(&c->visits, vi);
+  block_sync();  // every warp has folded its counters
+  if (threadIdx.x == 0) {
+    if (blockIdx.x == 0) {
+      s_ph[2] += global_ns() - s_tprev;
+      for (int k = 0; k < 6; ++k) atomicAdd(&c->phase_ns[k], s_ph[k]);
     }
+    atomicAdd(&c->edges, s_stat[0]);
+    atomicAdd(&c->ops, s_stat[1]);
+    atomicAdd(&c->arcs_read, s_stat[2]);
+    atomicAdd(&c->visits, s_stat[3]);
   }
 }
 
