@@ -580,11 +580,17 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
           const uint4 none = make_uint4(0u, 1u, kNoArc, 0u);
           uint4 a0 = make(0u);
           uint4 a1 = nsteps > 1u ? make(1u) : none;
-          if (a0.z != kNoArc) prefetch_l2(Dg + ((size_t)a0.x << LG));
+          // a vertex's line of the group: 32-256 bytes (two 128-byte lines for G = 64)
+          auto prefetch_line = [&](uint32_t v) {
+            const uint32_t *p = Dg + ((size_t)v << LG);
+            prefetch_l2(p);
+            if constexpr (GQ == 64) prefetch_l2(p + 32);
+          };
+          if (a0.z != kNoArc) prefetch_line(a0.x);
           for (uint32_t i = 0; i < nsteps; ++i) {
             sarc[lane] = a0;
             __syncwarp();
-            if (a1.z != kNoArc) prefetch_l2(Dg + ((size_t)a1.x << LG));
+            if (a1.z != kNoArc) prefetch_line(a1.x);
             const uint4 a2 = i + 2u < nsteps ? make(i + 2u) : none;
             if constexpr (GQ == 64)
               g_step64<QT>(a, sarc, sdv_g, dv_own, Dg_g, pend_g, dirty_g, lane, i32, chk);
