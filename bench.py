@@ -1325,6 +1325,24 @@ def run_rmat24(args):
             fg.check(fg.fg_sync(stream))
             result["plain_gpu"] = {"value": k / (a.elapsed_time(b) / 1000.0), "unit": UNIT,
                                    "sample": f"{k} sources, one query at a time (FG_MODE_PLAIN)"}
+            # BFS levels of the first timed step's sources with the same group size,
+            # two timed batches after a warm-up one, four rows checked against the oracle
+            ob = fg.fg_default_opts(group=int(opts.group))
+            s_b = src_d[0]
+            fg.check(fg.fg_bfs_batch(h, s_b, nb, out, stream, ob))
+            fg.check(fg.fg_sync(stream))
+            a.record(stream)
+            for _ in range(2):
+                fg.check(fg.fg_bfs_batch(h, s_b, nb, out, stream, ob))
+            b.record(stream)
+            fg.check(fg.fg_sync(stream))
+            bfs_ms = a.elapsed_time(b) / 2
+            kb = 4
+            ref_b = oracle.bfs(g, s_b[:kb].cpu().numpy())
+            result["bfs_same_batch"] = {
+                "value": nb / (bfs_ms / 1000.0), "unit": UNIT, "ms_per_batch": bfs_ms, "group": int(opts.group),
+                "exact_sampled": {"rows": kb, "exact": bool(np.array_equal(out[:kb].cpu().numpy().view(np.uint32),
+                                                                             ref_b))}}
             # parity of the timed path on a sampled row, and the CPU oracle on the host cores
             cores = oracle.num_threads()
             kc = args.cpu_sources or max(1, min(cores, 16))
