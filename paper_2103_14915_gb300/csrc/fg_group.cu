@@ -59,9 +59,18 @@ struct ItemDesc {
   uint32_t n;     // listed vertices (kItemPart) or steps of 32 arcs (kItemHub)
   uint32_t eb, ee;  // hub chunk: arc range
   uint32_t next;  // claim counter of the consumers (vertices or steps)
+  uint32_t ns;    // kItemPart: listed sparse vertices (few pending lanes)
+  uint32_t next_s;  // claim counter of the sparse vertices
   uint32_t pad;
   unsigned long long m;  // hub chunk: the lanes pending on the hub
 };
+
+// A listed vertex with at most kSparseT pending lanes is relaxed pair by pair:
+// a lane takes one (arc, pending query) pair and reads that query's 4-byte
+// value of the target, instead of the warp reading the target's whole line
+// for every arc. Lanes map to kSparseT slots per arc (32 / kSparseT arcs per
+// warp step).
+constexpr int kSparseT = 4;
 
 // Lane layout by group size. G <= 32: lane (h, g) holds query g of the group
 // for arc slot h (SL = 32 / G arcs per warp step), and a vertex's pending
@@ -473,7 +482,7 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
           if (ld_volatile_i32(&c->abort)) idx = n_hub + n_reg;
         }
         idx = __shfl_sync(kFull, idx, 0);
-        ItemDesc d{kItemEnd, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0ull};
+        ItemDesc d{kItemEnd, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0ull};
         if (idx < n_hub) {
           const uint4 itm = __ldcg(a.items + idx);
           const uint32_t e1 = G.rp[itm.y + 1];
@@ -524,20 +533,32 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
           // this round's masks of the item are taken: clear them for reuse
           for (int i = lane; i < ((S * MW) >> 2); i += 32)
             reinterpret_cast<uint4 *>(pm_g)[i] = make_uint4(0u, 0u, 0u, 0u);
-          // list the pending vertices with an arc
-          uint32_t cnt = 0;
+          // list the pending vertices with an arc: those with many pending
+          // lanes from the front of vid, the sparse ones (no window only)
+          // from its back
+          uint32_t cnt = 0, cnt_s = 0;
+          const bool use_sparse = GQ >= 32 && a.window == 0u;
+          const unsigned lt = (1u << lane) - 1u;
           for (int i0 = 0; i0 < S; i0 += 32) {
             const int i = i0 + lane;
             const uint32_t deg = rp_s[i + 1] - rp_s[i];
-            const bool keep = pm_s[i] != 0u && deg > 0u;
-            const unsigned bm = __ballot_sync(kFull, keep);
-            if (keep) vid_s[cnt + (uint32_t)__popc(bm & ((1u << lane) - 1u))] = (uint32_t)i;
-            cnt += (uint32_t)__popc(bm);
+            const M mk = pm_s[i];
+            const bool keep = mk != 0u && deg > 0u;
+            int pc;
+            if constexpr (GQ == 64) pc = __popcll(mk);
+            else pc = __popc(mk);
+            const bool sp = keep && use_sparse && pc <= kSparseT;
+            const unsigned bd = __ballot_sync(kFull, keep && !sp), bs = __ballot_sync(kFull, sp);
+            if (keep && !sp) vid_s[cnt + (uint32_t)__popc(bd & lt)] = (uint32_t)i;
+            if (sp) vid_s[S - 1 - (cnt_s + (uint32_t)__popc(bs & lt))] = (uint32_t)i;
+            cnt += (uint32_t)__popc(bd);
+            cnt_s += (uint32_t)__popc(bs);
           }
           d.kind = kItemPart;
           d.grp = grp;
           d.pv = p;
           d.n = cnt;
+          d.ns = cnt_s;
         }
         if (lane == 0) {
           s_desc[k] = d;
@@ -737,6 +758,95 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
             else
               run((tot + 31u) / 32u, make, static_cast<const uint32_t *>(sdv + g), kInf, __any_sync(kFull, big));
             __syncwarp();  // sdv is rewritten by the next batch
+          }
+          if constexpr (GQ >= 32) {
+            // the sparse vertices, 32 at a time: lanes take (arc, pending
+            // query) pairs, kSparseT slots per arc, and each pair reads and
+            // lowers one 4-byte value of its target
+            constexpr uint32_t kT = kSparseT, kAPS = 32 / kSparseT;  // slots per arc, arcs per step
+            uint32_t *sval = sdv;              // [32][kT] source values of the batch's vertices
+            uint32_t *sgq = sdv + 32u * kT;    // [32][kT] their queries
+            const int slog2 = G.slog2;
+            for (;;) {
+              uint32_t b0 = 0;
+              if (lane == 0) b0 = atomicAdd(&s_desc[k].next_s, 32u);
+              b0 = __shfl_sync(kFull, b0, 0);
+              if (b0 >= d.ns) break;
+              const uint32_t j = b0 + (uint32_t)lane;
+              const bool valid = j < d.ns;
+              const uint32_t li = valid ? vid_s[S - 1 - j] : 0u;
+              M mk = valid ? pm_s[li] : (M)0u;
+              const uint32_t a0 = valid ? rp_s[li] : 0u;
+              const uint32_t deg = valid ? rp_s[li + 1] - a0 : 0u;
+              // this lane's vertex: the values of its pending queries, in bit
+              // order (fresh from L2, as for the dense batches)
+              const uint32_t *Dv = Dg + ((size_t)(base + li) << LG);
+              uint32_t pc = 0;
+              bool near = false;
+              while (mk != 0u) {
+                int bp;
+                if constexpr (GQ == 64) bp = __ffsll((long long)mk) - 1;
+                else bp = __ffs(mk) - 1;
+                mk &= mk - 1u;
+                const uint32_t gq =
+                    GQ == 64 ? ((((uint32_t)bp & 31u) << 1) | ((uint32_t)bp >> 5)) : (uint32_t)bp;
+                const uint32_t dv = __ldcg(Dv + gq);
+                sval[lane * kT + pc] = dv;
+                sgq[lane * kT + pc] = gq;
+                near |= dv != kInf && dv >= ovf_lim;
+                ++pc;
+              }
+              r32 += deg * pc;  // this lane's vertex relaxes every arc for each pending query
+              const bool chk_s = __any_sync(kFull, near);
+              const uint32_t incl = warp_incl_scan(deg);
+              const uint32_t exd = incl - deg;
+              const uint32_t tot = __shfl_sync(kFull, incl, 31);
+              __syncwarp();
+              constexpr int kU = 4;  // steps with their loads in flight at once
+              for (uint32_t t0 = 0; t0 < tot; t0 += kAPS * kU) {
+                uint32_t nd[kU], cv[kU], gq[kU], vv[kU];
+                bool on[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                  const uint32_t t = t0 + u * kAPS + (uint32_t)lane / kT, slot = (uint32_t)lane % kT;
+                  const bool has = t < tot;
+                  const int L = owner_lane(exd, has ? t : 0u);
+                  const uint32_t pcL = __shfl_sync(kFull, pc, L);
+                  const uint32_t eL = __shfl_sync(kFull, a0, L) + (t - __shfl_sync(kFull, exd, L));
+                  a32 += (has && slot == 0u) ? 1u : 0u;  // the arc is read once, counted by its first slot
+                  on[u] = has && slot < pcL;
+                  nd[u] = kInf;
+                  cv[u] = 0u;
+                  gq[u] = 0u;
+                  vv[u] = 0u;
+                  if (on[u]) {
+                    const uint32_t v = __ldg(G.adj + eL);
+                    const uint32_t w = (QT != Q_BFS && G.wt != nullptr) ? __ldg(G.wt + eL) : 1u;
+                    const uint32_t dv = sval[L * kT + slot];
+                    gq[u] = sgq[L * kT + slot];
+                    uint32_t x = dv + w;
+                    if (QT != Q_BFS && chk_s && (x < dv || x == kInf)) {  // 2^32 - 1 reached
+                      atomicCAS(&c->status, 0, (int)FG_ERR_OVERFLOW);
+                      x = kInf - 1u;
+                    }
+                    nd[u] = x;
+                    vv[u] = v;
+                    cv[u] = Dg[((size_t)v << LG) + gq[u]];
+                  }
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                  if (on[u] && nd[u] < cv[u]) {  // a stale value is an upper bound, as in the dense step
+                    atomicMin(Dg + ((size_t)vv[u] << LG) + gq[u], nd[u]);
+                    atomicOr(pend_g + vv[u], group_bit<GQ>(gq[u]));
+                    dirty_g[vv[u] >> slog2] = 1u;
+                    ++i32;
+                    if constexpr (GQ != 64) gacc |= (uint32_t)group_bit<GQ>(gq[u]);
+                  }
+                }
+              }
+              __syncwarp();  // sval and sgq are rewritten by the next batch
+            }
           }
         }
         {
