@@ -1325,9 +1325,15 @@ def run_rmat24(args):
             fg.check(fg.fg_sync(stream))
             result["plain_gpu"] = {"value": k / (a.elapsed_time(b) / 1000.0), "unit": UNIT,
                                    "sample": f"{k} sources, one query at a time (FG_MODE_PLAIN)"}
-            # BFS levels of the first timed step's sources with the same group size,
-            # two timed batches after a warm-up one, four rows checked against the oracle
-            ob = fg.fg_default_opts(group=int(opts.group))
+            # BFS levels of the first timed step's sources, options from the
+            # autotuner on the same 64-source sample as the SSSP line, two timed
+            # batches after a warm-up one, four rows checked against the oracle
+            if args.no_tune:
+                ob = fg.fg_default_opts(group=int(opts.group))
+            else:
+                tune_src = torch.from_numpy(inputs.sources_uniform(g, 64, 4242)).to(dev)
+                st, ob, _ = fg.fg_tune_opts(h, fg.FG_QUERY_BFS, tune_src, 64, stream)
+                fg.check(st)
             s_b = src_d[0]
             fg.check(fg.fg_bfs_batch(h, s_b, nb, out, stream, ob))
             fg.check(fg.fg_sync(stream))
@@ -1340,7 +1346,7 @@ def run_rmat24(args):
             kb = 4
             ref_b = oracle.bfs(g, s_b[:kb].cpu().numpy())
             result["bfs_same_batch"] = {
-                "value": nb / (bfs_ms / 1000.0), "unit": UNIT, "ms_per_batch": bfs_ms, "group": int(opts.group),
+                "value": nb / (bfs_ms / 1000.0), "unit": UNIT, "ms_per_batch": bfs_ms, "group": int(ob.group),
                 "exact_sampled": {"rows": kb, "exact": bool(np.array_equal(out[:kb].cpu().numpy().view(np.uint32),
                                                                              ref_b))}}
             # parity of the timed path on a sampled row, and the CPU oracle on the host cores

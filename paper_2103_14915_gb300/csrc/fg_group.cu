@@ -307,6 +307,9 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
     const uint64_t pwords = 2ull * (uint64_t)a.ngroups * (uint64_t)a.npad * (uint64_t)MW;
     for (uint64_t i = tid; i < pwords / 4u; i += nthr) reinterpret_cast<uint4 *>(a.pend)[i] = make_uint4(0u, 0u, 0u, 0u);
     for (uint64_t i = tid; i < 2ull * K; i += nthr) a.dirty[i] = 0u;
+    if (a.reach)
+      for (uint64_t i = tid; i < (uint64_t)a.ngroups * (uint64_t)a.npad * (uint64_t)MW / 4u; i += nthr)
+        reinterpret_cast<uint4 *>(a.reach)[i] = make_uint4(0u, 0u, 0u, 0u);
     if (a.gbest)
       for (uint64_t i = tid; i < 2ull * (uint64_t)a.ngroups; i += nthr) a.gbest[i] = kInf;
     if (a.gact)
@@ -327,6 +330,7 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
     const uint32_t grp = (uint32_t)(q >> a.glog2), gq = (uint32_t)(q & (uint64_t)(Gq - 1));
     a.D[((size_t)grp * row + v) * (size_t)Gq + gq] = 0u;
     atomicOr(pend + (size_t)grp * row + v, group_bit<GQ>(gq));
+    if (a.reach) atomicOr(reinterpret_cast<M *>(a.reach) + (size_t)grp * row + v, group_bit<GQ>(gq));
     a.dirty[(size_t)grp * G.nparts + (v >> G.slog2)] = 1u;
     if (a.gbest) atomicMin(a.gbest + grp, 0u);
   }
@@ -399,6 +403,7 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
         uint32_t *Dg = a.D + (size_t)grp * row * (size_t)Gq;
         for (uint64_t v = tid; v < (uint64_t)G.n; v += nthr) {
           const uint64_t o = G.orig ? (uint64_t)G.orig[v] : v;
+          if (a.reach) a.reach[(size_t)grp * row + v] &= ~f;  // BFS: the lanes have reached nothing
           uint32_t bits = f;
           while (bits != 0u) {
             const int gg = __ffs(bits) - 1;
@@ -444,6 +449,10 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
           atomicOr(a.gact + (size_t)nxt * a.ngroups + grp, bit);
           atomicOr(a.occ + grp, bit);
           if (a.gbest) atomicMin(a.gbest + (size_t)nxt * a.ngroups + grp, 0u);
+          if (a.reach) {  // BFS: the source is reached; levels count from the next round
+            atomicOr(a.reach + (size_t)grp * row + v, bit);
+            a.lstart[sl] = round + 1u;
+          }
           ++admitted;
         }
         __syncwarp();
@@ -537,7 +546,7 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
           // lanes from the front of vid, the sparse ones (no window only)
           // from its back
           uint32_t cnt = 0, cnt_s = 0;
-          const bool use_sparse = GQ >= 32 && a.window == 0u;
+          const bool use_sparse = QT != Q_BFS && GQ >= 32 && a.window == 0u;
           const unsigned lt = (1u << lane) - 1u;
           for (int i0 = 0; i0 < S; i0 += 32) {
             const int i = i0 + lane;
@@ -622,7 +631,110 @@ __global__ void __launch_bounds__(kGThreads, 3) group_kernel(GroupArgs a) {
             a1 = a2;
           }
         };
-        if (d.kind == kItemHub) {
+        if constexpr (QT == Q_BFS) {
+          // BFS: rounds are levels, so a query's level of a vertex is fixed
+          // when the query first reaches it. reach[v] holds the queries that
+          // have reached v. A lane takes one arc at a time and sets the
+          // frontier lanes F of the arc's source that are new in the
+          // target's reach; only those lanes are marked pending and get
+          // their level. One 4- or 8-byte word per arc replaces the
+          // target's line.
+          M *reach_g = reinterpret_cast<M *>(a.reach) + (size_t)d.grp * row;
+          const int slog2 = G.slog2;
+          const uint32_t lvl = round + 1u;  // the level reached in this round (serve mode: minus the lane's start)
+          constexpr int kU = 4;  // arcs per lane with their loads in flight at once
+          // relax up to kU arcs per lane: targets v[u] (kNoArc: none) from frontiers F[u]
+          auto visit = [&](const uint32_t *v, const M *F) {
+            M nw[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) nw[u] = v[u] != kNoArc ? (F[u] & ~reach_g[v[u]]) : (M)0u;
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+              if (nw[u] == 0u) continue;
+              M fresh = nw[u] & ~atomicOr(reach_g + v[u], nw[u]);
+              if (fresh == 0u) continue;
+              atomicOr(pend_g + v[u], fresh);
+              dirty_g[v[u] >> slog2] = 1u;
+              if constexpr (GQ == 64) i32 += (uint32_t)__popcll(fresh);
+              else {
+                i32 += (uint32_t)__popc(fresh);
+                gacc |= fresh;
+              }
+              uint32_t *Dv = Dg + ((size_t)v[u] << LG);
+              while (fresh != 0u) {
+                int bp;
+                if constexpr (GQ == 64) bp = __ffsll((long long)fresh) - 1;
+                else bp = __ffs(fresh) - 1;
+                fresh &= fresh - 1u;
+                const uint32_t gq =
+                    GQ == 64 ? ((((uint32_t)bp & 31u) << 1) | ((uint32_t)bp >> 5)) : (uint32_t)bp;
+                Dv[gq] = a.lstart ? lvl - a.lstart[(size_t)d.grp * Gq + gq] : lvl;
+              }
+            }
+          };
+          if (d.kind == kItemHub) {
+            const M F = (M)d.m;
+            uint32_t fpc;
+            if constexpr (GQ == 64) fpc = (uint32_t)__popcll(F);
+            else fpc = (uint32_t)__popc(F);
+            for (;;) {
+              uint32_t s0 = 0;
+              if (lane == 0) s0 = atomicAdd(&s_desc[k].next, 4u);  // four steps of 32 arcs at a time
+              s0 = __shfl_sync(kFull, s0, 0);
+              if (s0 >= d.n) break;
+              uint32_t v[kU];
+              M Fs[kU];
+#pragma unroll
+              for (int u = 0; u < kU; ++u) {
+                const uint32_t e = d.eb + (s0 + (uint32_t)u) * 32u + (uint32_t)lane;
+                const bool has = s0 + (uint32_t)u < d.n && e < d.ee;
+                v[u] = has ? __ldg(G.adj + e) : kNoArc;
+                Fs[u] = F;
+                a32 += has ? 1u : 0u;
+                r32 += has ? fpc : 0u;
+              }
+              visit(v, Fs);
+            }
+          } else {
+            const uint32_t base = d.pv << G.slog2;
+            const uint32_t *rp_s = buf_rp(k), *vid_s = buf_vid(k);
+            const M *pm_s = buf_pm(k);
+            (void)base;
+            for (;;) {
+              uint32_t b0 = 0;
+              if (lane == 0) b0 = atomicAdd(&s_desc[k].next, 32u);
+              b0 = __shfl_sync(kFull, b0, 0);
+              if (b0 >= d.n) break;
+              const uint32_t j = b0 + (uint32_t)lane;
+              const bool valid = j < d.n;
+              const uint32_t li = valid ? vid_s[j] : 0u;
+              const M m = valid ? pm_s[li] : (M)0u;
+              const uint32_t a0 = valid ? rp_s[li] : 0u;
+              const uint32_t deg = valid ? rp_s[li + 1] - a0 : 0u;
+              if constexpr (GQ == 64) r32 += deg * (uint32_t)__popcll(m);
+              else r32 += deg * (uint32_t)__popc(m);
+              const uint32_t incl = warp_incl_scan(deg);
+              const uint32_t exd = incl - deg;
+              const uint32_t tot = __shfl_sync(kFull, incl, 31);
+              for (uint32_t t0 = 0; t0 < tot; t0 += 32u * kU) {
+                uint32_t v[kU];
+                M Fs[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                  const uint32_t t = t0 + (uint32_t)u * 32u + (uint32_t)lane;
+                  const bool has = t < tot;
+                  const int L = owner_lane(exd, has ? t : 0u);
+                  const uint32_t eL = __shfl_sync(kFull, a0, L) + (t - __shfl_sync(kFull, exd, L));
+                  const M FL = __shfl_sync(kFull, m, L);
+                  v[u] = has ? __ldg(G.adj + eL) : kNoArc;
+                  Fs[u] = FL;
+                  a32 += has ? 1u : 0u;
+                }
+                visit(v, Fs);
+              }
+            }
+          }
+        } else if (d.kind == kItemHub) {
           // this lane's value(s) of the hub, kInf where not pending
           using V = std::conditional_t<GQ == 64, uint2, uint32_t>;
           V dv;

@@ -63,7 +63,7 @@ struct IoSlot {
 
 struct Workspace {
   DevBuf cnt, prio, dirty, cur, pend, qbest, items, iprio, blocksum, e_key, e_op, b_op, ctrl;
-  DevBuf g_D, g_pend, g_dirty, g_items, g_best;  // group engine
+  DevBuf g_D, g_pend, g_dirty, g_items, g_best, g_reach;  // group engine
   DevBuf g_key, g_perm, g_psrc;                   // group engine: query order (two-hop reach)
   DevBuf scratch_r, scratch_c, scratch_p, state;
   DevBuf pl_dist, pl_rr, pl_pp, pl_cc, pl_stamp, pl_f0, pl_f1, pl_sizes;
@@ -73,7 +73,7 @@ struct Workspace {
   void release_all() {
     DevBuf *all[] = {&cnt, &prio, &dirty, &cur, &pend, &qbest, &items, &iprio, &blocksum, &e_key, &e_op,
                      &b_op, &ctrl, &scratch_r, &scratch_c, &scratch_p, &state, &pl_dist, &pl_rr,
-                     &pl_pp, &pl_cc, &pl_stamp, &pl_f0, &pl_f1, &pl_sizes, &g_D, &g_pend, &g_dirty,
+                     &pl_pp, &pl_cc, &pl_stamp, &pl_f0, &pl_f1, &pl_sizes, &g_D, &g_pend, &g_dirty, &g_reach,
                      &g_items, &g_best, &g_key, &g_perm, &g_psrc};
     for (DevBuf *b : all) b->release();
     io[0].release();

@@ -133,6 +133,8 @@ struct GroupArgs {
   uint32_t hub_chunk = 4096;      // arcs per hub chunk (a work item of its own)
   uint32_t window = 0;            // per-group value window of a round (0 = none)
   uint32_t *gbest = nullptr;      // [2][ngroups] smallest pending value per group (window scheduling)
+  uint32_t *reach = nullptr;      // BFS: [ngroups][npad] G-bit masks of the queries that reached each vertex
+  uint32_t *lstart = nullptr;     // BFS in serve mode: [slots] the round each lane's query started
   Ctrl *ctrl = nullptr;
   uint32_t max_rounds = 0;
   uint64_t watchdog_ns = 0;

@@ -564,10 +564,11 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
     {
       size_t free_b = 0, total_b = 0;
       CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-      const size_t held = ws.g_D.bytes + ws.g_pend.bytes + ws.g_dirty.bytes + ws.g_items.bytes + ws.g_best.bytes;
+      const size_t held = ws.g_D.bytes + ws.g_pend.bytes + ws.g_dirty.bytes + ws.g_items.bytes + ws.g_best.bytes +
+                          ws.g_reach.bytes;
       const double avail = 0.9 * (double)(free_b + held) - 512.0 * 1024 * 1024;
       const double mask_b = Gq == 64 ? 8.0 : 4.0;
-      const double per_group = (double)npad * 4.0 * (double)Gq + 2.0 * mask_b * (double)npad +
+      const double per_group = (double)npad * 4.0 * (double)Gq + (qtype == Q_BFS ? 3.0 : 2.0) * mask_b * (double)npad +
                                24.0 * (double)g->nparts + 20.0 * (double)g->hub_chunks + 8.0;
       int64_t cap_groups = std::max<int64_t>(1, (int64_t)(avail / per_group));
       const int64_t key_cap = (int64_t)(0xFFFFFFF0ull / (uint64_t)g->nparts);
@@ -589,6 +590,7 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
       return fail(FG_ERR_UNSUPPORTED, "too many work items for one launch; lower query_batch");
     CUDA_TRY(ws.g_D.reserve(4 * (size_t)ngroups_max * (size_t)npad * (size_t)Gq));
     CUDA_TRY(ws.g_pend.reserve((Gq == 64 ? 16 : 8) * (size_t)ngroups_max * (size_t)npad));
+    if (qtype == Q_BFS) CUDA_TRY(ws.g_reach.reserve((Gq == 64 ? 8 : 4) * (size_t)ngroups_max * (size_t)npad));
     CUDA_TRY(ws.g_dirty.reserve(8 * (size_t)ngroups_max * (size_t)g->nparts));
     // work items, then (G = 64) the upper mask words of the hub-chunk items
     CUDA_TRY(ws.g_items.reserve(16 * (size_t)(hub_cap + (uint64_t)ngroups_max * (uint64_t)g->nparts) +
@@ -635,6 +637,7 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
       a.hub_chunk = kHubChunk;
       a.window = qtype == Q_SSSP && o.sched == FG_SCHED_PRIORITY ? o.sched_window : 0u;
       a.gbest = a.window ? ws.g_best.as<uint32_t>() : nullptr;
+      a.reach = qtype == Q_BFS ? ws.g_reach.as<uint32_t>() : nullptr;
       a.ctrl = d_ctrl;
       a.max_rounds = max_rounds;
       a.watchdog_ns = watchdog_ns;

@@ -68,7 +68,7 @@ struct SlotLane {
   int G = 32, glog2 = 5, ngroups = 0, nslots = 0, blocks = 0, gi = 2;
   cudaStream_t stream = nullptr;
   cudaEvent_t done_ev = nullptr;
-  DevBuf D, pend, dirty, items, res, occ, seen, gact, ctrl;
+  DevBuf D, pend, dirty, items, res, occ, seen, gact, ctrl, reach, lstart;
   ServeBox *box = nullptr;        // mapped host memory (host address)
   ServeBox *box_dev = nullptr;    // its device address
   Ctrl *h_ctrl = nullptr;         // pinned copy of the control block after each launch
@@ -78,7 +78,7 @@ struct SlotLane {
   uint32_t round0 = 0;             // first round of the next launch (a launch yields after max_rounds)
   bool running = false, need_init = true;
   void release_all() {
-    DevBuf *all[] = {&D, &pend, &dirty, &items, &res, &occ, &seen, &gact, &ctrl};
+    DevBuf *all[] = {&D, &pend, &dirty, &items, &res, &occ, &seen, &gact, &ctrl, &reach, &lstart};
     for (DevBuf *b : all) b->release();
     if (box) cudaFreeHost(box);
     if (h_ctrl) cudaFreeHost(h_ctrl);
@@ -176,7 +176,7 @@ fg_status launch_lane(fg_server *s, Lane &L, int kind) {
 // vertex-major state, pending masks, dirty flags and work items, and its row.
 double per_slot_bytes(const fg_graph *g, int G) {
   const double npad = (double)g->nparts * (double)g->S;
-  return 4.0 * npad + (8.0 * npad + 24.0 * (double)g->nparts + 16.0 * (double)g->hub_chunks + 8.0) / (double)G +
+  return 4.0 * npad + (12.0 * npad + 24.0 * (double)g->nparts + 16.0 * (double)g->hub_chunks + 8.0) / (double)G +
          4.0 * (double)g->n;
 }
 
@@ -208,6 +208,10 @@ fg_status create_slot_lane(fg_server *s, SlotLane &C, int kind, int nslots, int 
   CUDA_TRY(C.occ.reserve(4 * ng));
   CUDA_TRY(C.seen.reserve(4 * (size_t)nslots));
   CUDA_TRY(C.gact.reserve(8 * ng));
+  if (C.qtype == Q_BFS) {
+    CUDA_TRY(C.reach.reserve(4 * ng * npad));
+    CUDA_TRY(C.lstart.reserve(4 * (size_t)nslots));
+  }
   CUDA_TRY(C.ctrl.reserve(sizeof(Ctrl)));
   const size_t box_bytes = sizeof(ServeBox) + sizeof(ServeSlot) * (size_t)(nslots - 1);
   void *hb = nullptr;
@@ -266,6 +270,8 @@ fg_status launch_slot_lane(fg_server *s, SlotLane &C) {
   a.seen = C.seen.as<uint32_t>();
   a.gact = C.gact.as<uint32_t>();
   a.init = C.need_init ? 1u : 0u;
+  a.reach = C.qtype == Q_BFS ? C.reach.as<uint32_t>() : nullptr;
+  a.lstart = C.qtype == Q_BFS ? C.lstart.as<uint32_t>() : nullptr;
   if (C.need_init) C.round0 = 0;
   a.round0 = C.round0;
   CUDA_TRY(launch_group(a, C.blocks, g->group_threads[C.gi], g->group_smem[C.gi], C.stream));
