@@ -1032,16 +1032,23 @@ __global__ void __launch_bounds__(256) group_out_kernel(const uint32_t *D, uint3
   }
 }
 
-// Two-hop reach of each query's source: the sum of its out-neighbours' degrees
-// (one warp per query; an out-of-range source gets 0 and is reported by the
-// engine's INIT).
+// Key of each query's source for its place in the batch: the sum of its
+// out-neighbours' degrees (two-hop reach), or, by_place, its internal id
+// counted down (queries from nearby sources side by side: partitions that
+// keep most arcs inside hold nearby vertices under consecutive ids). One warp
+// per query; an out-of-range source gets 0 and is reported by the engine's
+// INIT.
 __global__ void __launch_bounds__(256) group_key_kernel(DevGraph G, const int32_t *src, int32_t nq,
-                                                        unsigned long long *key) {
+                                                        unsigned long long *key, int by_place) {
   const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (q >= nq) return;
   const int32_t s = src[q];
   unsigned long long sum = 0;
+  if (s >= 0 && s < G.n && by_place) {
+    if (lane == 0) key[q] = (unsigned long long)(uint32_t)G.n - (G.intl ? (uint32_t)G.intl[s] : (uint32_t)s);
+    return;
+  }
   if (s >= 0 && s < G.n) {
     const uint32_t v = G.intl ? (uint32_t)G.intl[s] : (uint32_t)s;
     const uint32_t e0 = G.rp[v], e1 = G.rp[v + 1];
@@ -1136,11 +1143,11 @@ cudaError_t launch_group_out(const GroupArgs &a, uint32_t *out, const int32_t *r
   return cudaGetLastError();
 }
 
-cudaError_t launch_group_order(const DevGraph &g, const int32_t *src, int32_t nq, unsigned long long *key,
-                               int32_t *perm, int32_t *psrc, cudaStream_t s) {
+cudaError_t launch_group_order(const DevGraph &g, const int32_t *src, int32_t nq, bool by_place,
+                               unsigned long long *key, int32_t *perm, int32_t *psrc, cudaStream_t s) {
   if (nq <= 0) return cudaSuccess;
   const int64_t warps_grid = ((int64_t)nq * 32 + 255) / 256;
-  group_key_kernel<<<(unsigned)warps_grid, 256, 0, s>>>(g, src, nq, key);
+  group_key_kernel<<<(unsigned)warps_grid, 256, 0, s>>>(g, src, nq, key, by_place ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   group_rank_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(key, src, nq, perm, psrc);

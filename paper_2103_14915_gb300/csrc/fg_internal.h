@@ -181,10 +181,11 @@ bool group_fits(int S, int G);
 cudaError_t group_grid_size(int S, int G, int *blocks, int *threads, size_t *smem);
 cudaError_t launch_group(const GroupArgs &a, int blocks, int threads, size_t smem, cudaStream_t s);
 // Orders a batch's queries for the group engine: key[q] = arcs within two hops
-// of src[q]; perm[j] = the query in slot j (keys descending, ties by index),
-// psrc[j] = src[perm[j]]. key, perm and psrc hold nq entries each.
-cudaError_t launch_group_order(const DevGraph &g, const int32_t *src, int32_t nq, unsigned long long *key,
-                               int32_t *perm, int32_t *psrc, cudaStream_t s);
+// of src[q], or (by_place) the source's internal id counted down; perm[j] =
+// the query in slot j (keys descending, ties by index), psrc[j] =
+// src[perm[j]]. key, perm and psrc hold nq entries each.
+cudaError_t launch_group_order(const DevGraph &g, const int32_t *src, int32_t nq, bool by_place,
+                               unsigned long long *key, int32_t *perm, int32_t *psrc, cudaStream_t s);
 // group-engine state (internal order, vertex-major in groups) -> caller's query-major rows
 // Writes the launch's rows to out: slot j's row to out[rowmap[j] * n], or to
 // out[j * n] when rowmap is null.

@@ -608,7 +608,11 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
       CUDA_TRY(ws.g_key.reserve(8 * (size_t)nq));
       CUDA_TRY(ws.g_perm.reserve(4 * (size_t)nq));
       CUDA_TRY(ws.g_psrc.reserve(4 * (size_t)nq));
-      CUDA_TRY(launch_group_order(g->dg, src, (int32_t)nq, ws.g_key.as<unsigned long long>(), ws.g_perm.as<int32_t>(),
+      // graphs whose partitions keep most arcs inside (road-like): nearby
+      // sources together; else sources of alike reach together
+      const bool by_place = !(g->m > 0 && 2 * g->cut > g->m);
+      CUDA_TRY(launch_group_order(g->dg, src, (int32_t)nq, by_place, ws.g_key.as<unsigned long long>(),
+                                  ws.g_perm.as<int32_t>(),
                                   ws.g_psrc.as<int32_t>(), stream));
       launches += 2;
       gsrc = ws.g_psrc.as<int32_t>();
