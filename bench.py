@@ -1028,11 +1028,22 @@ def run_configs(args):
     print(json.dumps(res), flush=True)
 
 
+def code_sha256_16(path) -> str:
+    """SHA-256 prefix of a C++/CUDA source with its // comments and blank lines
+    removed, so that a comment edit does not count as a change of the kernel."""
+    import re
+    lines = []
+    for ln in path.read_text().splitlines():
+        ln = re.sub(r"//.*$", "", ln).rstrip()
+        if ln.strip():
+            lines.append(ln)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
+
+
 def kernel_traffic(profile: str, source: str):
     """DRAM bytes per launch from a committed ncu summary, while the kernel source it
-    was taken from is unchanged (else None)."""
-    src = (ROOT / "paper_2103_14915_gb300" / "csrc" / source).read_bytes()
-    sha = hashlib.sha256(src).hexdigest()[:16]
+    was taken from is unchanged apart from comments (else None)."""
+    sha = code_sha256_16(ROOT / "paper_2103_14915_gb300" / "csrc" / source)
     f = ROOT / "profiles" / profile
     if not f.exists():
         return None

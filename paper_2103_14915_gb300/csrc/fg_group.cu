@@ -1,5 +1,5 @@
 // Group engine: the buffered loop of Alg. 2 for SSSP and BFS with queries
-// processed in groups of G (8, 16 or 32), one lane per query.
+// processed in groups of G (8, 16, 32 or 64; one query per lane, two for 64).
 //
 // Why groups. On graphs whose partitions are cut by almost every arc (power-law
 // graphs with the paper's random equal-vertex partitions, Sec. 6.1), nearly
@@ -37,6 +37,16 @@
 // Round r reads pend[r & 1] and dirty[r & 1] and writes pend[(r + 1) & 1] and
 // dirty[(r + 1) & 1]; a (partition, group)'s masks of round r are cleared by
 // its visit, a hub's by the scan, so both halves are zero again when reused.
+//
+// Three relaxation forms share this loop. Dense (SSSP): the warp reads a
+// target's line for each arc and every pending lane compares its value.
+// Sparse (SSSP, a vertex with at most kSparseT pending lanes): each lane
+// takes one (arc, query) pair and reads that single value. Bitwise (BFS):
+// rounds are levels, so a lane takes one arc and sets the source's frontier
+// lanes in the target's reach mask; the lanes that were new get their level.
+// The host orders a batch's queries before it cuts them into groups, by
+// two-hop reach, or by source position on road-like graphs, so that the
+// queries of a group advance alike.
 #include <cstdio>
 #include <type_traits>
 
