@@ -1040,9 +1040,10 @@ def code_sha256_16(path) -> str:
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
 
 
-def kernel_traffic(profile: str, source: str):
+def kernel_traffic(profile: str, source: str, sources: int, group: int):
     """DRAM bytes per launch from a committed ncu summary, while the kernel source it
-    was taken from is unchanged apart from comments (else None)."""
+    was taken from is unchanged apart from comments and the launch is the captured
+    one (sources per launch, group size); else None."""
     sha = code_sha256_16(ROOT / "paper_2103_14915_gb300" / "csrc" / source)
     f = ROOT / "profiles" / profile
     if not f.exists():
@@ -1053,6 +1054,8 @@ def kernel_traffic(profile: str, source: str):
             k, v = ln.split(":", 1)
             kv[k.strip()] = v.strip()
     if kv.get("source_sha256_16") != sha:
+        return None
+    if kv.get("capture_sources") != str(sources) or kv.get("capture_group") != str(group):
         return None
     try:
         return float(kv["dram_bytes_per_launch"])
@@ -1260,8 +1263,9 @@ def run_rmat24(args):
     alg_bytes = out_bytes + arc_bytes + op_bytes
     kern_ms = statistics.mean(batch_ms)
     achieved = alg_bytes / (kern_ms / 1000.0) / 1e9
-    kernel = "fg::group_kernel<0>" if group > 1 else "fg::engine_kernel<0>"
-    traffic = kernel_traffic("group_kernel_rmat24_traffic.txt", "fg_group.cu") if group > 1 else None
+    kernel = f"fg::group_kernel<0, {group}>" if group > 1 else "fg::engine_kernel<0>"
+    traffic = (kernel_traffic("group_kernel_rmat24_traffic.txt", "fg_group.cu", nb, group)
+               if group > 1 and not args.graph_scale else None)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": f"{peak_kind} hbm_gbs (STREAM-style copy)", "kernel": kernel,
                 "algorithmic_bytes_per_launch": alg_bytes,
