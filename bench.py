@@ -1145,7 +1145,9 @@ def serving_extra(fg, inputs, requests=300, lambdas=(2000.0, 50000.0)):
     st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, fg.fg_default_graph_opts())
     fg.check(st)
     try:
-        opts = {0: {"group": 32}, 1: {"group": 32}}
+        # batch lanes: SSSP in groups of 64, BFS in groups of 32 (a 64-query batch
+        # is one group); slot lanes take 32 (the largest group of the serve mode)
+        opts = {0: {"group": 64}, 1: {"group": 32}}
         runs = [serve_stream(fg, h, g, lam, requests, seed=int(lam), lanes=4, max_batch=64, kinds=(0, 1, 2),
                              alpha=0.15, eps=1e-6, opts=opts) for lam in lambdas]
         # slot-level batching: SSSP and BFS join running launches lane by lane,
