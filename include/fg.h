@@ -115,8 +115,10 @@ typedef struct {
                                and one read of the arcs serve the whole group (best where almost
                                every arc leaves its partition: power-law graphs); 1 = one query
                                per warp and visit (best on road-like graphs, whose partitions
-                               keep most arcs inside). 0 (default) = automatic: 16 when more
-                               than half of the graph's arcs cross partitions, else 1. PPR
+                               keep most arcs inside). 0 (default) = automatic: when more than
+                               half of the graph's arcs cross partitions, 64 for SSSP (32 with a
+                               sched_window) and 32 for BFS (a smaller batch takes the smallest
+                               group that holds it), else 1. PPR
                                always runs one query per warp. In the group engine, sched_window
                                (SSSP) bounds each round to values below the group's smallest
                                pending value plus the window (groups of 8 to 32 only: a group of

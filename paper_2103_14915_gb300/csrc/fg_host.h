@@ -162,6 +162,13 @@ namespace fg {
 constexpr uint32_t kHubMin = 512;     // group engine: vertices with more arcs are hubs
 constexpr uint32_t kHubChunk = 4096;  // group engine: arcs per hub chunk
 
+// The query group that fg_opts.group = 0 resolves to for a batch of nq
+// queries of one kind: on graphs whose partitions are cut by more than half
+// of the arcs, 64 for SSSP (32 under a window) and 32 for BFS (the smallest of
+// 8, 16, 32, 64 that holds a smaller batch, and one that fits shared memory);
+// else 1.
+int auto_group_size(const fg_graph *g, int qtype, int64_t nq, bool windowed);
+
 // One batch of nq queries on workspace ws (see fg_runtime.cpp).
 fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div, int qtype, const int32_t *src_in,
                        int32_t nq, uint32_t *dist_in, float alpha, float eps, float *p_in, float *r_in,

@@ -548,10 +548,9 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
   // query group: one lane per query (group engine) where most arcs leave their
   // partition, else one warp per query and visit; PPR is never grouped
   int Gq = 1;
-  if (qtype != Q_PPR && o.mode == FG_MODE_BUFFERED) {
-    if (o.group == 0) Gq = (g->m > 0 && 2 * g->cut > g->m) ? 16 : 1;
-    else Gq = o.group;
-  }
+  if (qtype != Q_PPR && o.mode == FG_MODE_BUFFERED)
+    Gq = o.group == 0 ? auto_group_size(g, qtype, nq, o.sched == FG_SCHED_PRIORITY && o.sched_window != 0u)
+                      : o.group;
 
   if (o.mode == FG_MODE_BUFFERED && Gq > 1) {
     int glog2 = 0;
@@ -899,6 +898,14 @@ extern "C" fg_status fg_sync(void *stream_v) {
 }
 
 namespace fg {
+
+int auto_group_size(const fg_graph *g, int qtype, int64_t nq, bool windowed) {
+  if (!(g->m > 0 && 2 * g->cut > g->m)) return 1;
+  int G = (qtype == Q_BFS || windowed) ? 32 : 64;  // groups of 64 run FIFO rounds only
+  while (G > 8 && (int64_t)(G / 2) >= nq) G /= 2;  // a small batch: the smallest group that holds it
+  while (G > 8 && !group_fits(g->S, G)) G /= 2;
+  return group_fits(g->S, G) ? G : 1;
+}
 
 fg_status report_error(fg_status s, const char *msg) {
   t_err = msg ? msg : "";

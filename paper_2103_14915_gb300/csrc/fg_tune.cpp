@@ -119,8 +119,8 @@ extern "C" fg_status fg_tune_opts_ex(fg_graph *g, int32_t kind, const int32_t *s
     ms = t;
     return FG_OK;
   };
-  // the query group (the default resolves to 16 on cut-dominated graphs, else 1)
-  const int auto_group = (g->m > 0 && 2 * g->cut > g->m) ? 16 : 1;
+  // the query group (what the default resolves to is measured already)
+  const int auto_group = auto_group_size(g, kind == FG_QUERY_BFS ? Q_BFS : Q_SSSP, nq, false);
   if (kind != FG_QUERY_PPR) {
     for (int G : {1, 16, 32, 64}) {
       if (G == auto_group || (G > 1 && !group_fits(g->S, G))) continue;
