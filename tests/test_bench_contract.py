@@ -60,3 +60,28 @@ def test_step_sources_cover_the_list_before_repeating():
     allv = np.concatenate(seen)
     assert len(np.unique(allv)) == 1000  # ten blocks of 100, each once
     assert np.array_equal(bench.step_sources(srcs, 0, 2, 5, 100), seen[0])  # then the list wraps
+
+
+def test_traffic_record_matches_code_not_comments(tmp_path, monkeypatch):
+    """The committed ncu traffic record is used only for the kernel code it was
+    taken from (a comment edit keeps it, a code edit drops it) and only for the
+    captured launch (sources per launch, group size)."""
+    sys.path.insert(0, str(ROOT))
+    import bench
+    csrc = tmp_path / "paper_2103_14915_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    src = csrc / "k.cu"
+    src.write_text("// header\n__global__ void k(int *p) {\n  p[0] = 1;  // store\n}\n")
+    sha = bench.code_sha256_16(src)
+    (prof / "t.txt").write_text(f"# note: a: b\nsource_sha256_16: {sha}\ncapture_sources: 256\ncapture_group: 64\n"
+                                "dram_bytes_per_launch: 1000\n")
+    monkeypatch.setattr(bench, "ROOT", tmp_path)
+    assert bench.kernel_traffic("t.txt", "k.cu", 256, 64) == 1000.0
+    assert bench.kernel_traffic("t.txt", "k.cu", 128, 64) is None
+    assert bench.kernel_traffic("t.txt", "k.cu", 256, 32) is None
+    src.write_text("// another header\n\n__global__ void k(int *p) {\n  p[0] = 1;\n}\n")  # comments only
+    assert bench.kernel_traffic("t.txt", "k.cu", 256, 64) == 1000.0
+    src.write_text("__global__ void k(int *p) {\n  p[0] = 2;\n}\n")  # the code changed
+    assert bench.kernel_traffic("t.txt", "k.cu", 256, 64) is None
