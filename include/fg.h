@@ -246,7 +246,7 @@ enum { FG_QUERY_SSSP = 0, FG_QUERY_BFS = 1, FG_QUERY_PPR = 2 };
  * Autotuner. The paper tunes its scheduling and yield parameters by hand per
  * graph (Sec. 5, Tab. 4); here the host times candidate fg_opts for one query
  * kind (FG_QUERY_*, declared below) on a sample batch and writes the fastest
- * to *best: the default; for SSSP and BFS the query group (1, 16 or 32; see
+ * to *best: the default; for SSSP and BFS the query group (1, 16, 32 or 64; see
  * fg_opts.group); then, with one query per warp, FG_SCHED_PRIORITY windows from
  * wide to narrow -- multiples of the graph's mean arc weight for SSSP, levels
  * for BFS -- until one takes more than twice the best time, delta (yield
