@@ -124,11 +124,13 @@ typedef struct {
                                pending value plus the window (groups of 8 to 32 only: a group of
                                64 with a window is FG_ERR_UNSUPPORTED); delta, bucket,
                                yield_edges, emit_capacity and threads_per_vertex do not apply */
-    int32_t group_order;    /* group engine: 0 (default) = the batch's queries are ordered by the
-                               number of arcs within two hops of their source, largest first,
-                               before they are cut into groups, so that a group's queries reach
-                               the same vertices in the same rounds and share more of each
-                               partition visit (results still go to the caller's rows);
+    int32_t group_order;    /* group engine: 0 (default) = the batch's queries are ordered before
+                               they are cut into groups, so that a group's queries reach the same
+                               vertices in the same rounds and share more of each partition
+                               visit: by the number of arcs within two hops of their source,
+                               largest first, or, on graphs whose partitions keep most arcs
+                               inside, by source position (results still go to the caller's rows;
+                               batches of more than 65,536 queries keep their order);
                                1 = groups follow the order of src */
     int32_t check_staging;  /* group engine self-test: 1 = after each shared-memory staging wait,
                                compare every staged row offset and pending mask with global

@@ -600,7 +600,8 @@ fg_status run_batch_on(fg_graph *g, Workspace &ws, bool shared_ws, int grid_div,
     CUDA_TRY(cudaMemsetAsync(d_ctrl, 0, sizeof(Ctrl), stream));
     // queries ordered by two-hop reach, so each group's (and each launch's)
     // queries advance through the graph in step; rows go back to the caller's order
-    const bool reorder = o.group_order == 0 && nq > Gq;
+    // (the rank kernel compares every pair of queries: batches up to 2^16)
+    const bool reorder = o.group_order == 0 && nq > Gq && nq <= 65536;
     const int32_t *gsrc = src;
     const int32_t *rowmap = nullptr;
     if (reorder) {
