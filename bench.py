@@ -50,9 +50,10 @@ GRID_DESC = ("road-like 2D grid 1024x1024 (1,048,576 vertices), 4-neighbour edge
 GRID_NQ = 1024
 SOURCE_SETS = 3
 # Scheduling for the grid workload (per-query priority windows, i.e. Delta-stepping
-# across partitions; chosen by the sweep recorded in the design notes)
+# across partitions, with yield heuristic 2's delta for SSSP): what fg_tune_opts
+# picks on the workload's 1,024 sources (window 10x and delta 5x the mean weight)
 TUNED_BFS = {"sched": 1, "sched_window": 24}
-TUNED_SSSP = {"sched": 1, "sched_window": 50000}
+TUNED_SSSP = {"sched": 1, "sched_window": 50490, "delta": 25245}
 
 
 def parse():

@@ -141,7 +141,11 @@ extern "C" fg_status fg_tune_opts_ex(fg_graph *g, int32_t kind, const int32_t *s
         if ((st = try_opts(o)) != FG_OK) return st;
       }
     }
-  } else if (kind != FG_QUERY_PPR) {  // PPR buffers are scheduled first-in first-out
+  }
+  if (kind != FG_QUERY_PPR) {  // PPR buffers are scheduled first-in first-out
+    // one query per warp with per-query windows, from wide to narrow, against
+    // whatever has won so far: a FIFO group engine can beat one query per
+    // warp in FIFO rounds on a road-like graph and still lose to its windows
     std::vector<double> windows;
     if (kind == FG_QUERY_BFS || !g->weighted) {
       const double lv[] = {64, 48, 32, 24, 16, 12, 8, 4, 2};
@@ -156,6 +160,7 @@ extern "C" fg_status fg_tune_opts_ex(fg_graph *g, int32_t kind, const int32_t *s
       if (w == last) continue;
       last = w;
       fg_opts o = base;
+      o.group = 1;
       o.sched = FG_SCHED_PRIORITY;
       o.sched_window = w;
       st = time_batch(g, kind, src, nq, out.p, nullptr, stream, o, alpha, eps, ea, eb_, &ms);
@@ -170,7 +175,7 @@ extern "C" fg_status fg_tune_opts_ex(fg_graph *g, int32_t kind, const int32_t *s
     }
     // yield heuristic 2 on top of the chosen window: values beyond (first value
     // + delta) wait for a later visit
-    if (pick.sched == FG_SCHED_PRIORITY) {
+    if (pick.group == 1 && pick.sched == FG_SCHED_PRIORITY) {
       const uint32_t w = pick.sched_window;
       for (uint32_t dl : {w / 2u, w / 4u}) {
         if (dl == 0u) continue;
@@ -185,7 +190,7 @@ extern "C" fg_status fg_tune_opts_ex(fg_graph *g, int32_t kind, const int32_t *s
         }
       }
     }
-    if (g->max_degree <= 8) {
+    if (pick.group == 1 && g->max_degree <= 8) {
       fg_opts o = pick;
       o.threads_per_vertex = 1;
       st = time_batch(g, kind, src, nq, out.p, nullptr, stream, o, alpha, eps, ea, eb_, &ms);
