@@ -69,6 +69,8 @@ def parse():
                     help="plumbing tests only: a smaller R-MAT of the same recipe instead of scale 24")
     ap.add_argument("--no-ppr-check", action="store_true", help="skip the R-MAT s22 PPR error record")
     ap.add_argument("--no-grid-extra", action="store_true", help="skip the grid workload extra key")
+    ap.add_argument("--no-group-sweep", action="store_true",
+                    help="--ablation: skip the group-size sweep on the R-MAT s24 bench workload")
     ap.add_argument("--no-serving-extra", action="store_true", help="skip the R-MAT s25 serving extra key")
     ap.add_argument("--cpu-sources", type=int, default=0,
                     help="sources of the CPU oracle sample (default: one per host core, at most 16)")
@@ -492,7 +494,8 @@ def run_ablation(args):
             cfgs += [("lane-per-vertex expansion", dict(TUNED_BFS, threads_per_vertex=1),
                       dict(TUNED_SSSP, threads_per_vertex=1)),
                      ("group engine G=16 (lanes = queries)", {"group": 16}, {"group": 16}),
-                     ("group engine G=32 (lanes = queries)", {"group": 32}, {"group": 32})]
+                     ("group engine G=32 (lanes = queries)", {"group": 32}, {"group": 32}),
+                     ("group engine G=64 (two queries per lane)", {"group": 64}, {"group": 64})]
         for name, ob, os_ in cfgs:
             row = {"S": S, "partition": "grow" if method == fg.FG_PART_GROW else "range", "config": name,
                    "cut_arcs": int(info.cut_arcs)}
@@ -507,7 +510,49 @@ def run_ablation(args):
             rows.append(row)
             print(json.dumps(row), file=sys.stderr, flush=True)
         fg.fg_graph_destroy(h)
-    print(json.dumps({"metric": "ablation", "workload": GRID_WORKLOAD, "sources": nq, "rows": rows}), flush=True)
+    groups = [] if args.no_group_sweep else group_sweep_rmat24(fg, inputs, dev)
+    print(json.dumps({"metric": "ablation", "workload": GRID_WORKLOAD, "sources": nq, "rows": rows,
+                      "rmat24_groups": groups}), flush=True)
+
+
+def group_sweep_rmat24(fg, inputs, dev):
+    """Group sizes and the query order on the bench workload (R-MAT s24, the first
+    256 sources of the bench line's list): one warm-up and one timed batch of SSSP
+    and of BFS per setting, FIFO rounds, every result compared with the first
+    setting's (rows identical whatever the group or order)."""
+    import torch
+    g = inputs.workload_graph(WORKLOAD)
+    src = torch.from_numpy(step_sources(inputs.workload_sources(WORKLOAD, g), 0, 1, 0, NQ_STEP)).to(dev)
+    nq = src.numel()
+    st, h = fg.fg_graph_create_ex(g.n, g.m, g.row_ptr, g.col, g.w, 0, fg.fg_default_graph_opts())
+    fg.check(st)
+    out = torch.empty((nq, g.n), dtype=torch.int32, device=dev)
+    rows, ref = [], {}
+    try:
+        for group, order in ((16, 0), (32, 1), (32, 0), (64, 1), (64, 0)):
+            row = {"group": group, "group_order": "as given" if order else "two-hop reach"}
+            for kind, f in (("sssp", fg.fg_sssp_batch), ("bfs", fg.fg_bfs_batch)):
+                o = fg.fg_default_opts(group=group, group_order=order)
+                fg.check(f(h, src, nq, out, None, o))
+                fg.check(fg.fg_sync())
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fg.check(f(h, src, nq, out, None, o))
+                b.record()
+                fg.check(fg.fg_sync())
+                torch.cuda.synchronize()
+                d = fg.fg_stats(h)[1].as_dict()
+                if kind not in ref:
+                    ref[kind] = out.cpu()
+                ms = a.elapsed_time(b)
+                row[kind] = {"ms": round(ms, 1), "qps": round(nq / (ms / 1000.0), 1), "rounds": d["rounds"],
+                             "arcs_read": d["arcs_read"], "lane_relaxations": d["edges"],
+                             "same_result": bool(torch.equal(out.cpu(), ref[kind]))}
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+    finally:
+        fg.fg_graph_destroy(h)
+    return rows
 
 
 def run_ncp(args):
